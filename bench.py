@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark: compact cell-updates/s of the life step on the Sierpinski
+triangle F^{3,2} at r = 20 (3.49e9 compact cells, Bernoulli(0.3) seed 3,
+B3/S23) on one GB300, with its HBM roofline fraction, next to the
+bounding-box step at r = 16 (the largest level whose box fits), the
+end-to-end call from host buffers, and the CPU oracle on the host cores.
+
+One benchmark step is one generation of the whole hot path over the whole
+state: for every compact cell lambda, the Moore probe, nu and the rule
+(one launch of the tiled step kernel).  Inputs are already resident in HBM
+when the timed region starts; the state (3.49 GB per buffer) is far larger
+than the 129 MB L2, so no flush is needed between iterations of the
+headline; the r = 16 compact comparison fits in L2 and is timed with an L2
+flush between generations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compact cell-updates/s (Sierpinski triangle r=20, B3/S23) and % HBM roofline vs bounding box on 1 GB300"
+UNIT = "cell-updates/s"
+KERNEL_SRC = os.path.join(ROOT, "paper_2110_12952_gb300", "csrc", "step.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--r", type=int, default=20, help="triangle level of the headline workload")
+    ap.add_argument("--bb-r", type=int, default=16, help="level of the compact-vs-BB comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-bb", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy kernel)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 copy measurement)"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("step.cu", "internal.cuh", "handle.h"):
+        with open(os.path.join(ROOT, "paper_2110_12952_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; None otherwise."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+        if d.get("kernel_hash") != kernel_hash() or d.get("workload") != workload:
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        rows = []
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(r: int, target_s: float, seed: int, p: float):
+    """Time the oracle's compact step on the first 3^L cells of the level-r
+    triangle (one level-L subtree; its neighbours lie in the first 3^(L+1)
+    cells, which are initialised from the same seeded generator).  L is
+    chosen from a short calibration so that the sample takes ~target_s."""
+    import numpy as np
+    import oracle
+    from paper_2110_12952_gb300 import workloads as W
+    fam = W.TRIANGLE
+    o = oracle.Fractal(fam.k, fam.s, r, fam.dim, fam.table())
+    st = np.zeros(o.cells, dtype=np.uint8)   # untouched pages stay unmapped
+    out = np.zeros(o.cells, dtype=np.uint8)
+    Lc = min(11, r - 1)
+    o.init_bernoulli(seed, p, 0, 3 ** (Lc + 1), out=st)
+    t0 = time.perf_counter()
+    o.step_range(st, 0, 3 ** Lc, out=out)
+    rate = 3 ** Lc / max(time.perf_counter() - t0, 1e-6)
+    L = Lc
+    while L + 1 < r and 3 ** (L + 1) / rate <= target_s:
+        L += 1
+    o.init_bernoulli(seed, p, 0, 3 ** (L + 1), out=st)
+
+    def run():
+        t = time.perf_counter()
+        o.step_range(st, 0, 3 ** L, out=out)
+        return time.perf_counter() - t
+
+    return o, L, run
+
+
+def cpu_baseline(r, target_s, seed, p):
+    import oracle
+    o, L, run = oracle_sample(r, target_s, seed, p)
+    dt = run()
+    return {"value": 3 ** L / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"one generation of the first 3^{L} = {3 ** L} compact cells (one level-{L} "
+                      f"subtree) of the triangle r={r}, seed {seed}, p={p}; {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores on the same workload and metric."""
+    import oracle
+    from paper_2110_12952_gb300 import workloads as W
+    inst = W.TRI_R20 if args.r == 20 else W.Instance(W.TRIANGLE, args.r, 0.3, 3, 1000)
+    if rank != 0:
+        return None
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    o, L, run = oracle_sample(inst.r, per_step, inst.seed, inst.p)
+    for _ in range(args.warmup):
+        run()
+    total = sum(run() for _ in range(args.steps))
+    value = 3 ** L * args.steps / total
+    sample = (f"each step: one generation of the first 3^{L} = {3 ** L} compact cells (a level-{L} "
+              f"subtree) of the triangle r={inst.r}")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": workload_config(inst),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def workload_config(inst):
+    return {"workload": f"sierpinski_triangle_F32_r{inst.r}", "fractal": "F^{3,2} offsets (0,0),(1,0),(0,1)",
+            "r": inst.r, "cells": 3 ** inst.r, "p": inst.p, "seed": inst.seed, "rule": "B3/S23",
+            "generations_per_step": 1,
+            "l2": "state per buffer larger than the 129 MB L2; no flush needed"}
+
+
+# ------------------------------------------------------------------- GPU
+
+def time_steps(fn, steps, warmup, flush=None):
+    """Per-iteration CUDA-event times (ms) on the current stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    st = torch.cuda.current_stream()
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+    from paper_2110_12952_gb300 import Fractal, build, workloads as W
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    inst = W.TRI_R20 if args.r == 20 else W.Instance(W.TRIANGLE, args.r, 0.3, 3, 1000)
+    fam = inst.family
+    g = Fractal.from_family(fam, inst.r)
+    a = g.init_bernoulli(inst.seed + rank, inst.p)
+    b = torch.empty_like(a)
+    bufs = [a, b]
+    cur = [0]
+
+    def one_generation():
+        g.step(bufs[cur[0]], out=bufs[1 - cur[0]], steps=1)
+        cur[0] ^= 1
+
+    # warm-up, then exactly K timed generations bracketed by barrier + sync
+    for _ in range(args.warmup):
+        one_generation()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one_generation()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    total_units = g.cells * args.steps * world
+    value = total_units / (ms_max / 1e3)
+    ms_per_step = ms_max / args.steps
+
+    # roofline of the step kernel: 2 algorithmic bytes per compact update
+    peak, peak_src = measured_peak()
+    alg_bytes = 2.0 * g.cells
+    achieved = alg_bytes / (ms / args.steps / 1e3) / 1e9
+    workload = workload_config(inst)["workload"]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_per_launch(workload), "kernel": "step_tiled_kernel<2>",
+            "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src,
+            "tile_levels": g.tile_levels}
+
+    extra = {}
+    # end-to-end through the public API from pinned host buffers
+    if not args.no_e2e:
+        host_in = torch.empty(g.cells, dtype=torch.uint8).pin_memory()
+        host_out = torch.empty(g.cells, dtype=torch.uint8).pin_memory()
+        host_in.copy_(bufs[cur[0]])
+        e2e_steps = max(1, min(args.steps, 5))
+        g.run_host(host_in, host_out, steps=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            g.run_host(host_in, host_out, steps=1)
+        dt = (time.perf_counter() - t0) / e2e_steps
+        extra["e2e"] = {"value": g.cells / dt, "unit": UNIT, "h2d_bytes_per_step": g.cells,
+                        "d2h_bytes_per_step": g.cells, "ms_per_step": dt * 1e3,
+                        "call": "fractal_run_host (H2D, 1 generation, D2H, sync)"}
+        del host_in, host_out
+    del a, b, bufs
+    g.close()
+    torch.cuda.empty_cache()
+
+    # compact vs bounding box at equal r
+    if not args.no_bb and rank == 0:
+        extra["bb_compare"] = bb_compare(args, W)
+
+    gpu_launches = args.steps  # one step-kernel launch per generation
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": dict(workload_config(inst), parallelism=f"replicas{world}"),
+            "roofline": roof, "gpu_launches": gpu_launches}
+    cs = clocks.summary()
+    line["clocks"] = cs
+    line.update(extra)
+    return line
+
+
+def bb_compare(args, W):
+    import torch
+    from paper_2110_12952_gb300 import Fractal
+    r = args.bb_r
+    inst = W.Instance(W.TRIANGLE, r, 0.3, 2, 1000)
+    g = Fractal.from_family(inst.family, r)
+    peak, _ = measured_peak()
+    flush_buf = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1)
+
+    st = g.init_bernoulli(inst.seed, inst.p)
+    out = torch.empty_like(st)
+    n = max(5, min(args.steps, 20))
+    ct = time_steps(lambda: g.step(st, out=out, steps=1), n, 3, flush=flush)
+    box = g.scatter(st)
+    box_out = torch.empty_like(box)
+    bt = time_steps(lambda: g.bb_step(box, out=box_out, steps=1), n, 3)
+    c_ms, b_ms = statistics.median(ct), statistics.median(bt)
+    res = {"workload": f"sierpinski_triangle_F32_r{r}", "cells": g.cells, "box_cells": g.box_cells,
+           "compact_updates_per_s": g.cells / (c_ms / 1e3),
+           "compact_ms_per_generation": c_ms,
+           "compact_hbm_frac": 2.0 * g.cells / (c_ms / 1e3) / 1e9 / peak,
+           "compact_note": "state 43 MB per buffer fits in L2; L2 flushed (512 MB write) before each timed generation",
+           "bb_ms_per_generation": b_ms,
+           "bb_compact_updates_per_s": g.cells / (b_ms / 1e3),
+           "bb_box_updates_per_s": g.box_cells / (b_ms / 1e3),
+           "bb_hbm_frac": 2.0 * g.box_cells / (b_ms / 1e3) / 1e9 / peak,
+           "speedup_compact_vs_bb": b_ms / c_ms,
+           "memory_ratio_bb_vs_compact": g.box_cells / g.cells,
+           "generations_timed": n}
+    del st, out, box, box_out, flush_buf
+    g.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    line = run_ours(args, rank, world, dist)
+    if rank == 0:
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args.r, args.cpu_seconds, 3, 0.3)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

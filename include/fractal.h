@@ -1,0 +1,164 @@
+/*
+ * fractal.h -- C ABI of the GB300 library for cellular automata on NBB
+ * fractals kept in compact storage (Quezada & Navarro, "Accelerating Compact
+ * Fractals with Tensor Core GPUs", 2021).
+ *
+ * Terms (all from the paper):
+ *   NBB fractal F_n^{k,s} (Sec. 1): level m+1 is k translated, non-rotated,
+ *     non-overlapping copies of level m on an s-times larger grid; level 0 is
+ *     one cell.  At level r the bounding box has side n = s^r and the fractal
+ *     has V = k^r cells (Eq. 1).
+ *   transition table: offsets[j*dim + i] in [0,s) is the position, in units
+ *     of s^m, of replica j along axis i; j is the replica ID of Sec. 3.1.
+ *   compact index omega = sum_mu d_mu k^mu, where d_mu is the replica ID at
+ *     level mu (mu = 0 is the finest level).  Compact state buffers hold one
+ *     byte per cell in this order (k^r bytes).
+ *   lambda(omega) (Sec. 1, Sec. 3): compact index -> embedded coordinate
+ *     p = sum_mu s^mu offsets[d_mu].
+ *   nu(p) (Sec. 3.1, Eqs. 2-8): embedded coordinate -> compact index, or -1
+ *     ("outside") when p is off the fractal or outside the box.
+ *   box: the n^dim bounding box, one byte per cell, x fastest, then y, z.
+ *
+ * Conventions for every call:
+ *   - Return value: FR_OK (0) or a negative FR_E* code; a readable message
+ *     for the calling thread is available from fractal_last_error().
+ *   - Buffers passed as `dev` are device pointers that the caller allocates,
+ *     owns and keeps alive until the call's work on `stream` has finished.
+ *     Buffers passed as `host` are host pointers (pinned memory is fastest).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Work is enqueued asynchronously; errors raised by a
+ *     kernel while it runs surface at the next call or at fractal_sync().
+ *   - Input states: any nonzero byte is alive.  Output states are exactly
+ *     0 or 1.
+ *   - Rules are life-like: bit c of birth_mask (survive_mask) gives the new
+ *     state of a dead (live) cell with c live Moore neighbours (8 in 2D, 26
+ *     in 3D).  Neighbours outside the box or off the fractal are dead; there
+ *     is no wrap-around.  B3/S23 is birth 0x8, survive 0xC.
+ *   - Handles are not thread-safe: one host thread per handle at a time.
+ *     Different handles may be used concurrently.
+ */
+#ifndef FRACTAL_H
+#define FRACTAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FR_OK = 0,
+    FR_EINVAL = -1,     /* bad argument (null pointer, aliasing, bad table) */
+    FR_EOVERFLOW = -2,  /* k^r, s^r or n^dim beyond the supported range    */
+    FR_ENOMEM = -3,     /* device or host allocation failed                */
+    FR_ECUDA = -4,      /* a CUDA runtime call failed                      */
+    FR_ETIMEOUT = -5,   /* a bounded device-side wait gave up              */
+    FR_EBUSY = -6,      /* resource (server slot, memory budget) exhausted */
+    FR_ENOTFOUND = -7   /* unknown request or instance id                  */
+};
+
+typedef struct fractal fractal_t;
+
+/* Message describing the last error raised on the calling thread ("" if
+ * none).  The pointer stays valid until the thread's next library call. */
+const char *fractal_last_error(void);
+
+/* Library version string. */
+const char *fractal_version(void);
+
+/* Build a fractal handle (Sec. 1 definition, Eq. 1 volume).
+ *   k        number of replicas per level, 1 <= k <= s^dim
+ *   s        growth ratio per level, 2 <= s <= 16, and s^dim <= 256
+ *   r        scale level, r >= 0; requires s^r < 2^31 and k^r < 2^62
+ *   dim      2 or 3
+ *   offsets  host array of k*dim int32 values in [0,s), rows pairwise
+ *            distinct; row j is replica j.  Copied; not retained.
+ *   out      receives the handle (owned by the caller, freed by
+ *            fractal_destroy).
+ * Errors: FR_EINVAL for a bad table, FR_EOVERFLOW for sizes out of range. */
+int fractal_create(int k, int s, int r, int dim, const int32_t *offsets,
+                   fractal_t **out);
+
+/* Free a handle and the device memory it owns (tables, scratch).  Waits for
+ * the handle's outstanding work.  NULL is accepted. */
+int fractal_destroy(fractal_t *f);
+
+/* cells = k^r (Eq. 1), side = n = s^r; either pointer may be NULL. */
+int fractal_info(const fractal_t *f, int64_t *cells, int64_t *side);
+
+/* lambda (Sec. 3): coords_dev[e*dim + i] = axis i of lambda(omega_dev[e]),
+ * for e < count.  Every omega must be in [0, k^r); others give FR_EINVAL at
+ * the next call (their coordinates are written as -1). */
+int fractal_lambda(const fractal_t *f, const int64_t *omega_dev, int64_t count,
+                   int32_t *coords_dev, void *stream);
+
+/* nu (Sec. 3.1, Eqs. 2-8 with the inverse transition table as H):
+ * omega_dev[e] = compact index of the cell at coords_dev[e*dim ..], or -1
+ * when that cell is outside the box or off the fractal. */
+int fractal_nu(const fractal_t *f, const int32_t *coords_dev, int64_t count,
+               int64_t *omega_dev, void *stream);
+
+/* The paper's multi-dimensional compact coordinate (Eqs. 6-8): component
+ * (mu mod dim) gains H_mu * k^floor(mu/dim) at each level mu.  In 2D this is
+ * (nu_x, nu_y) on a k^ceil(r/2) x k^floor(r/2) rectangle.  Outside cells give
+ * -1 in every component.  compact_dev has count*dim entries. */
+int fractal_nu2d(const fractal_t *f, const int32_t *coords_dev, int64_t count,
+                 int64_t *compact_dev, void *stream);
+
+/* Seeded Bernoulli(p) compact state (not from the paper; synthetic input):
+ * state_dev[omega] = 1 iff the top 53 bits of the omega-th SplitMix64 output
+ * for `seed` (mix(seed + (omega+1)*0x9e3779b97f4a7c15)) are below
+ * floor(p * 2^53).  p is clamped to [0,1].  state_dev has k^r bytes. */
+int fractal_init_bernoulli(const fractal_t *f, uint8_t *state_dev,
+                           uint64_t seed, double p, void *stream);
+
+/* The stencil step of Sec. 3, repeated `steps` times (synchronous
+ * generations, Sec. 4 benchmark): every compact cell omega takes
+ * lambda(omega), counts its live Moore neighbours through nu, and applies
+ * the rule.  in_dev and out_dev are k^r-byte compact states that must not
+ * overlap; in_dev is never written.  steps = 0 copies (normalised to 0/1).
+ * For steps > 1 the library ping-pongs through its own scratch buffer of k^r
+ * bytes, allocated on first need and kept until fractal_destroy. */
+int fractal_step(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
+                 int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
+                 void *stream);
+
+/* The bounding-box approach (Sec. 4, "BB"): the same rule applied to every
+ * cell of the n^dim box.  Cells off the fractal count as dead whatever their
+ * byte and are written as 0.  box_in_dev / box_out_dev: n^dim bytes each,
+ * not overlapping.  Scratch for steps > 1 as in fractal_step (n^dim bytes). */
+int fractal_bb_step(fractal_t *f, const uint8_t *box_in_dev, uint8_t *box_out_dev,
+                    int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
+                    void *stream);
+
+/* Compact <-> box views (through lambda).  scatter writes every box byte:
+ * box_dev[lambda(omega)] = compact_dev[omega] != 0, and 0 off the fractal.
+ * gather: compact_dev[omega] = box_dev[lambda(omega)] != 0. */
+int fractal_scatter_to_box(const fractal_t *f, const uint8_t *compact_dev,
+                           uint8_t *box_dev, void *stream);
+int fractal_gather_from_box(const fractal_t *f, const uint8_t *box_dev,
+                            uint8_t *compact_dev, void *stream);
+
+/* End-to-end call from host memory: copies host_in (k^r bytes) to the device,
+ * runs fractal_step for `steps` generations and copies the result to
+ * host_out (k^r bytes), all on `stream`, and waits for it.  Device buffers
+ * are owned by the handle (allocated on first use, reused, freed by
+ * fractal_destroy). */
+int fractal_run_host(fractal_t *f, const uint8_t *host_in, uint8_t *host_out,
+                     int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
+                     void *stream);
+
+/* Tile depth used by fractal_step: a tile is the k^L cells that share their
+ * digits above level L (one subtree).  L = -1 restores the automatic choice.
+ * fractal_get_tile_levels reports the depth the next step will use. */
+int fractal_set_tile_levels(fractal_t *f, int levels);
+int fractal_get_tile_levels(const fractal_t *f, int *levels);
+
+/* Waits for `stream` and reports any asynchronous CUDA error. */
+int fractal_sync(void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRACTAL_H */

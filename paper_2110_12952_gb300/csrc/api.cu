@@ -1,0 +1,271 @@
+// api.cu -- C ABI entry points: handle creation and validation, error
+// reporting, multi-step ping-pong and host-buffer calls.  Kernels live in
+// maps.cu (lambda, nu, init, scatter/gather), step.cu (compact step) and
+// bb.cu (bounding-box step).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+namespace fr {
+
+static thread_local std::string g_err;
+
+void set_error(int code, const std::string &msg)
+{
+    (void)code;
+    g_err = msg;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(FR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return FR_ENOMEM;
+    return FR_ECUDA;
+}
+
+static int fail(int code, const std::string &msg)
+{
+    set_error(code, msg);
+    return code;
+}
+
+static bool mul_ok(int64_t a, int64_t b, int64_t limit, int64_t *out)
+{
+    if (a != 0 && b > limit / a) return false;
+    *out = a * b;
+    return true;
+}
+
+int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st);
+
+}  // namespace fr
+
+using namespace fr;
+
+extern "C" const char *fractal_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *fractal_version(void) { return "compact-fractal-ca 0.1 (sm_103a)"; }
+
+extern "C" int fractal_create(int k, int s, int r, int dim, const int32_t *offsets,
+                              fractal_t **out)
+{
+    g_err.clear();
+    if (!out) return fail(FR_EINVAL, "fractal_create: out is NULL");
+    *out = nullptr;
+    if (!offsets) return fail(FR_EINVAL, "fractal_create: offsets is NULL");
+    if (dim != 2 && dim != 3) return fail(FR_EINVAL, "fractal_create: dim must be 2 or 3");
+    if (s < 2 || s > 16) return fail(FR_EINVAL, "fractal_create: s must be in [2,16]");
+    if (r < 0) return fail(FR_EINVAL, "fractal_create: r must be >= 0");
+    int sd = 1;
+    for (int i = 0; i < dim; ++i) sd *= s;
+    if (sd > kMaxSD) return fail(FR_EINVAL, "fractal_create: s^dim must be <= 256");
+    if (k < 1 || k > sd) return fail(FR_EINVAL, "fractal_create: k must be in [1, s^dim]");
+    std::vector<int> seen(sd, -1);
+    for (int j = 0; j < k; ++j) {
+        int t = 0, m = 1;
+        for (int i = 0; i < dim; ++i) {
+            int v = offsets[j * dim + i];
+            if (v < 0 || v >= s)
+                return fail(FR_EINVAL, "fractal_create: offset component outside [0,s)");
+            t += v * m;
+            m *= s;
+        }
+        if (seen[t] >= 0) return fail(FR_EINVAL, "fractal_create: duplicate offset rows");
+        seen[t] = j;
+    }
+    int64_t cells = 1, side = 1;
+    for (int i = 0; i < r; ++i) {
+        if (!mul_ok(cells, k, (int64_t)1 << 62, &cells))
+            return fail(FR_EOVERFLOW, "fractal_create: k^r >= 2^62");
+        if (!mul_ok(side, s, ((int64_t)1 << 31) - 1, &side))
+            return fail(FR_EOVERFLOW, "fractal_create: s^r >= 2^31");
+    }
+    int64_t box = 1;
+    for (int i = 0; i < dim; ++i)
+        if (!mul_ok(box, side, INT64_MAX, &box)) { box = -1; break; }
+
+    fractal *f = new (std::nothrow) fractal();
+    if (!f) return fail(FR_ENOMEM, "fractal_create: out of host memory");
+    f->k = k; f->s = s; f->r = r; f->dim = dim;
+    f->offsets.assign(offsets, offsets + (size_t)k * dim);
+    f->cells = cells;
+    f->side = side;
+    f->box_cells = box;
+    FracDev &D = f->dev;
+    memset(&D, 0, sizeof(D));
+    D.k = k; D.s = s; D.r = r; D.dim = dim; D.sd = sd;
+    D.sdiv = make_div((uint32_t)s);
+    D.kdiv = make_div((uint32_t)(k >= 2 ? k : 2));
+    for (int t = 0; t < kMaxSD; ++t) D.hinv[t] = -1;
+    for (int t = 0; t < sd; ++t) D.hinv[t] = (int16_t)seen[t];
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < dim; ++i) D.off[j][i] = (int8_t)offsets[j * dim + i];
+    cudaError_t e = cudaGetDevice(&f->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, f->device);
+    if (e != cudaSuccess) {
+        delete f;
+        return cuda_fail(e, "fractal_create: no usable CUDA device");
+    }
+    *out = f;
+    return FR_OK;
+}
+
+extern "C" int fractal_destroy(fractal_t *f)
+{
+    g_err.clear();
+    if (!f) return FR_OK;
+    cudaDeviceSynchronize();
+    free_step_plan(f->plan);
+    free_bb_plan(f->bb);
+    cudaFree(f->scratch);
+    cudaFree(f->bb_scratch);
+    cudaFree(f->host_io[0]);
+    cudaFree(f->host_io[1]);
+    delete f;
+    return FR_OK;
+}
+
+extern "C" int fractal_info(const fractal_t *f, int64_t *cells, int64_t *side)
+{
+    g_err.clear();
+    if (!f) return fail(FR_EINVAL, "fractal_info: handle is NULL");
+    if (cells) *cells = f->cells;
+    if (side) *side = f->side;
+    return FR_OK;
+}
+
+extern "C" int fractal_set_tile_levels(fractal_t *f, int levels)
+{
+    g_err.clear();
+    if (!f) return fail(FR_EINVAL, "fractal_set_tile_levels: handle is NULL");
+    if (levels < -1 || levels > f->r)
+        return fail(FR_EINVAL, "fractal_set_tile_levels: levels must be -1 or in [0, r]");
+    if (levels != f->tile_levels_user) {
+        f->tile_levels_user = levels;
+        cudaDeviceSynchronize();
+        free_step_plan(f->plan);
+    }
+    return FR_OK;
+}
+
+extern "C" int fractal_get_tile_levels(const fractal_t *f, int *levels)
+{
+    g_err.clear();
+    if (!f || !levels) return fail(FR_EINVAL, "fractal_get_tile_levels: NULL argument");
+    int rc = ensure_step_plan(const_cast<fractal_t *>(f));
+    if (rc) return rc;
+    *levels = f->plan.L;
+    return FR_OK;
+}
+
+static bool overlap(const void *a, const void *b, int64_t n)
+{
+    const uint8_t *x = (const uint8_t *)a, *y = (const uint8_t *)b;
+    return x < y + n && y < x + n;
+}
+
+static int ensure_buffer(uint8_t **buf, int64_t bytes, const char *what)
+{
+    if (*buf) return FR_OK;
+    cudaError_t e = cudaMalloc((void **)buf, (size_t)bytes);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        return cuda_fail(e, what);
+    }
+    return FR_OK;
+}
+
+// Ping-pong `steps` generations so that the last one lands in `out`: step i
+// (1-based) writes `out` when steps - i is even, the scratch buffer otherwise.
+template <class Launch>
+static int run_generations(const uint8_t *in, uint8_t *out, uint8_t *scratch, int64_t steps,
+                           Launch launch)
+{
+    const uint8_t *src = in;
+    for (int64_t i = 1; i <= steps; ++i) {
+        uint8_t *dst = ((steps - i) % 2 == 0) ? out : scratch;
+        int rc = launch(src, dst);
+        if (rc) return rc;
+        src = dst;
+    }
+    return FR_OK;
+}
+
+extern "C" int fractal_step(fractal_t *f, const uint8_t *in, uint8_t *out, int64_t steps,
+                            uint32_t birth, uint32_t survive, void *stream)
+{
+    g_err.clear();
+    if (!f || !in || !out) return fail(FR_EINVAL, "fractal_step: NULL argument");
+    if (steps < 0) return fail(FR_EINVAL, "fractal_step: steps < 0");
+    if (overlap(in, out, f->cells)) return fail(FR_EINVAL, "fractal_step: in and out overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (steps == 0) return launch_copy_normalise(in, out, f->cells, st);
+    int rc = ensure_step_plan(f);
+    if (rc) return rc;
+    if (steps > 1) {
+        rc = ensure_buffer(&f->scratch, f->cells, "fractal_step: scratch allocation");
+        if (rc) return rc;
+    }
+    return run_generations(in, out, f->scratch, steps, [&](const uint8_t *a, uint8_t *b) {
+        return launch_step_once(f, a, b, birth, survive, st);
+    });
+}
+
+extern "C" int fractal_bb_step(fractal_t *f, const uint8_t *in, uint8_t *out, int64_t steps,
+                               uint32_t birth, uint32_t survive, void *stream)
+{
+    g_err.clear();
+    if (!f || !in || !out) return fail(FR_EINVAL, "fractal_bb_step: NULL argument");
+    if (steps < 0) return fail(FR_EINVAL, "fractal_bb_step: steps < 0");
+    if (f->box_cells < 0) return fail(FR_EOVERFLOW, "fractal_bb_step: n^dim overflows");
+    if (overlap(in, out, f->box_cells))
+        return fail(FR_EINVAL, "fractal_bb_step: in and out overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_bb_plan(f);
+    if (rc) return rc;
+    if (steps == 0) {
+        // zero generations: the masked, normalised box (no births; every
+        // live member survives whatever its count)
+        return launch_bb_once(f, in, out, 0u, 0xffffffffu, st);
+    }
+    if (steps > 1) {
+        rc = ensure_buffer(&f->bb_scratch, f->box_cells, "fractal_bb_step: scratch allocation");
+        if (rc) return rc;
+    }
+    return run_generations(in, out, f->bb_scratch, steps, [&](const uint8_t *a, uint8_t *b) {
+        return launch_bb_once(f, a, b, birth, survive, st);
+    });
+}
+
+extern "C" int fractal_run_host(fractal_t *f, const uint8_t *host_in, uint8_t *host_out,
+                                int64_t steps, uint32_t birth, uint32_t survive, void *stream)
+{
+    g_err.clear();
+    if (!f || !host_in || !host_out) return fail(FR_EINVAL, "fractal_run_host: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_buffer(&f->host_io[0], f->cells, "fractal_run_host: device buffer");
+    if (!rc) rc = ensure_buffer(&f->host_io[1], f->cells, "fractal_run_host: device buffer");
+    if (rc) return rc;
+    FR_CUDA(cudaMemcpyAsync(f->host_io[0], host_in, (size_t)f->cells, cudaMemcpyHostToDevice, st));
+    rc = fractal_step(f, f->host_io[0], f->host_io[1], steps, birth, survive, stream);
+    if (rc) return rc;
+    FR_CUDA(cudaMemcpyAsync(host_out, f->host_io[1], (size_t)f->cells, cudaMemcpyDeviceToHost, st));
+    FR_CUDA(cudaStreamSynchronize(st));
+    return FR_OK;
+}
+
+extern "C" int fractal_sync(void *stream)
+{
+    g_err.clear();
+    FR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    FR_CUDA(cudaGetLastError());
+    return FR_OK;
+}

@@ -1,0 +1,78 @@
+// handle.h -- the fractal_t handle and the launch plans shared by the .cu
+// files of the library (internal; not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace fr {
+
+// Tiled compact step (Sec. 3 stencil procedure, done per subtree).
+// A tile is the k^L cells whose digits above level L agree: one level-L
+// subtree, contiguous in omega, whose cells fill an s^L-wide box in the
+// embedding.  The local lambda table `pos` (identical for every tile) gives
+// each cell's offset in a shared-memory box padded by one halo cell per side.
+struct StepPlan {
+    int L = -1;            // tile levels
+    int64_t KL = 0;        // k^L cells per tile
+    int64_t NT = 0;        // k^(r-L) tiles
+    int B = 0;             // s^L, tile box side
+    int P = 0;             // B + 2, padded side
+    int box_bytes = 0;     // P^dim rounded up to 16
+    int coarse_levels = 0; // r - L
+    int nring = 0;         // halo cells to fetch per tile
+    uint32_t *pos = nullptr;   // [KL] box offset of local cell l
+    uint32_t *ring = nullptr;  // [2*nring] (box offset | dir << 24, local omega)
+    int smem = 0;          // dynamic shared memory per CTA
+    int block = 256;
+    int grid = 0;
+};
+
+// Bounding-box step (Sec. 4 "BB"): membership of a box cell is decided from
+// two bitmaps, the lowest Lb levels (local) and the levels above (coarse).
+struct BBPlan {
+    int Lb = -1;
+    int S = 0;             // s^Lb, local side
+    int C = 0;             // s^(r-Lb), coarse side
+    uint32_t *local_bits = nullptr;   // S^dim bits, x fastest
+    uint32_t *coarse_bits = nullptr;  // C^dim bits, x fastest
+    int64_t local_words = 0, coarse_words = 0;
+};
+
+}  // namespace fr
+
+struct fractal {
+    int k = 0, s = 0, r = 0, dim = 0;
+    std::vector<int32_t> offsets;
+    int64_t cells = 0;     // k^r
+    int64_t side = 0;      // s^r
+    int64_t box_cells = 0; // side^dim, or -1 when it overflows int64
+    fr::FracDev dev{};
+    int device = 0;
+    int num_sms = 0;
+    int tile_levels_user = -1;
+    fr::StepPlan plan;
+    fr::BBPlan bb;
+    uint8_t *scratch = nullptr;      // k^r bytes, ping-pong for steps > 1
+    uint8_t *bb_scratch = nullptr;   // n^dim bytes, ping-pong for BB steps > 1
+    uint8_t *host_io[2] = {nullptr, nullptr};  // device buffers of run_host
+};
+
+namespace fr {
+
+int ensure_step_plan(fractal *f);
+int ensure_bb_plan(fractal *f);
+void free_step_plan(StepPlan &p);
+void free_bb_plan(BBPlan &p);
+
+int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
+                     uint32_t survive, cudaStream_t st);
+int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
+                   uint32_t survive, cudaStream_t st);
+int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st);
+
+}  // namespace fr

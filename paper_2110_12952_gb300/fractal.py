@@ -1,0 +1,163 @@
+"""Python binding of the compact-fractal library: the same calls as the C ABI
+(``include/fractal.h``), taking PyTorch CUDA tensors and the current stream.
+
+This module only marshals arguments; every map, step and copy runs in
+``libfractal.so``.  PyTorch provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+from .workloads import Family, LIFE_B3S23, default_rule
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev_ptr(t: torch.Tensor, dtype, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+class Fractal:
+    """Handle on an NBB fractal F^{k,s} at level r (``fractal_create``)."""
+
+    def __init__(self, k: int, s: int, r: int, dim: int, offsets):
+        self._lib = capi.load()
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(k * dim))
+        h = capi.c_fp()
+        capi.check(self._lib.fractal_create(k, s, r, dim, off.ctypes.data_as(capi.c_i32p),
+                                            ctypes.byref(h)), self._lib)
+        self._h = h
+        self.k, self.s, self.r, self.dim = k, s, r, dim
+        self.offsets = off.reshape(k, dim).copy()
+        cells, side = ctypes.c_int64(), ctypes.c_int64()
+        capi.check(self._lib.fractal_info(h, ctypes.byref(cells), ctypes.byref(side)), self._lib)
+        self.cells, self.side = cells.value, side.value
+        self.box_cells = self.side ** dim
+
+    @classmethod
+    def from_family(cls, fam: Family, r: int) -> "Fractal":
+        return cls(fam.k, fam.s, r, fam.dim, fam.table())
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fractal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc):
+        return capi.check(rc, self._lib)
+
+    # -------------------------------------------------------------- maps
+    def lam(self, omega: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        n = omega.numel()
+        out = out if out is not None else torch.empty((n, self.dim), dtype=torch.int32, device=omega.device)
+        self._check(self._lib.fractal_lambda(self._h, _dev_ptr(omega, torch.int64, "omega"), n,
+                                             _dev_ptr(out, torch.int32, "coords"), _stream(stream)))
+        return out
+
+    def nu(self, coords: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        n = coords.numel() // self.dim
+        out = out if out is not None else torch.empty(n, dtype=torch.int64, device=coords.device)
+        self._check(self._lib.fractal_nu(self._h, _dev_ptr(coords, torch.int32, "coords"), n,
+                                         _dev_ptr(out, torch.int64, "omega"), _stream(stream)))
+        return out
+
+    def nu2d(self, coords: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        n = coords.numel() // self.dim
+        out = out if out is not None else torch.empty((n, self.dim), dtype=torch.int64, device=coords.device)
+        self._check(self._lib.fractal_nu2d(self._h, _dev_ptr(coords, torch.int32, "coords"), n,
+                                           _dev_ptr(out, torch.int64, "compact"), _stream(stream)))
+        return out
+
+    # ------------------------------------------------------------- states
+    def empty_state(self, device="cuda") -> torch.Tensor:
+        return torch.empty(self.cells, dtype=torch.uint8, device=device)
+
+    def init_bernoulli(self, seed: int, p: float, out: torch.Tensor | None = None, stream=None):
+        out = out if out is not None else self.empty_state()
+        self._check(self._lib.fractal_init_bernoulli(self._h, _dev_ptr(out, torch.uint8, "state"),
+                                                     seed & (2**64 - 1), float(p), _stream(stream)))
+        return out
+
+    def step(self, state: torch.Tensor, out: torch.Tensor | None = None, steps: int = 1,
+             rule=None, stream=None) -> torch.Tensor:
+        birth, survive = rule if rule is not None else self.default_rule()
+        out = out if out is not None else torch.empty_like(state)
+        self._check(self._lib.fractal_step(self._h, _dev_ptr(state, torch.uint8, "state_in"),
+                                           _dev_ptr(out, torch.uint8, "state_out"), steps,
+                                           birth, survive, _stream(stream)))
+        return out
+
+    def bb_step(self, box: torch.Tensor, out: torch.Tensor | None = None, steps: int = 1,
+                rule=None, stream=None) -> torch.Tensor:
+        birth, survive = rule if rule is not None else self.default_rule()
+        out = out if out is not None else torch.empty_like(box)
+        self._check(self._lib.fractal_bb_step(self._h, _dev_ptr(box, torch.uint8, "box_in"),
+                                              _dev_ptr(out, torch.uint8, "box_out"), steps,
+                                              birth, survive, _stream(stream)))
+        return out
+
+    def scatter(self, compact: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        out = out if out is not None else torch.empty(self.box_cells, dtype=torch.uint8, device=compact.device)
+        self._check(self._lib.fractal_scatter_to_box(self._h, _dev_ptr(compact, torch.uint8, "compact"),
+                                                     _dev_ptr(out, torch.uint8, "box"), _stream(stream)))
+        return out
+
+    def gather(self, box: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        out = out if out is not None else torch.empty(self.cells, dtype=torch.uint8, device=box.device)
+        self._check(self._lib.fractal_gather_from_box(self._h, _dev_ptr(box, torch.uint8, "box"),
+                                                      _dev_ptr(out, torch.uint8, "compact"), _stream(stream)))
+        return out
+
+    def run_host(self, host_in: torch.Tensor, host_out: torch.Tensor, steps: int = 1, rule=None,
+                 stream=None):
+        """End-to-end call from host buffers (``fractal_run_host``)."""
+        birth, survive = rule if rule is not None else self.default_rule()
+        for t, name in ((host_in, "host_in"), (host_out, "host_out")):
+            if t.is_cuda or t.dtype != torch.uint8 or not t.is_contiguous() or t.numel() != self.cells:
+                raise TypeError(f"{name} must be a contiguous host uint8 tensor of {self.cells} cells")
+        self._check(self._lib.fractal_run_host(self._h, host_in.data_ptr(), host_out.data_ptr(), steps,
+                                               birth, survive, _stream(stream)))
+        return host_out
+
+    # ------------------------------------------------------------- tuning
+    @property
+    def tile_levels(self) -> int:
+        v = ctypes.c_int()
+        self._check(self._lib.fractal_get_tile_levels(self._h, ctypes.byref(v)))
+        return v.value
+
+    @tile_levels.setter
+    def tile_levels(self, levels: int):
+        self._check(self._lib.fractal_set_tile_levels(self._h, int(levels)))
+
+    def default_rule(self):
+        return (0x20, 0x30) if self.dim == 3 else LIFE_B3S23
+
+    def sync(self, stream=None):
+        self._check(self._lib.fractal_sync(_stream(stream)))

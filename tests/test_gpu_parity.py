@@ -1,0 +1,296 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+All of this is integer work, so the bar is bit-exact equality everywhere.
+Small levels are compared exhaustively (every omega, every box coordinate,
+every output cell, several tile depths, so that tiles, halos and ragged
+tails are all exercised); the full-size workloads are compared on seeded
+samples the oracle computes one by one, after one and after several
+generations, in the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_12952_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2110_12952_gb300 import build
+    build.build()
+    import paper_2110_12952_gb300 as pkg
+    return pkg
+
+
+def gpu_fr(P, fam, r):
+    return P.Fractal.from_family(fam, r)
+
+
+def ora(fam, r):
+    return oracle.Fractal(fam.k, fam.s, r, fam.dim, fam.table())
+
+
+def all_coords(side, dim, margin=0):
+    lo, hi = -margin, side + margin
+    ax = np.arange(lo, hi, dtype=np.int64)
+    g = np.meshgrid(*([ax] * dim), indexing="ij")
+    return np.stack([x.reshape(-1) for x in g[::-1]], axis=1)
+
+
+def rule_of(fam):
+    return W.default_rule(fam)
+
+
+def oracle_rule(fam):
+    b, s = rule_of(fam)
+    return oracle.Rule(b, s)
+
+
+SMALL = [(W.TRIANGLE, 7), (W.CARPET, 4), (W.VICSEK, 4), (W.MENGER, 3), (W.FULL_SQUARE, 5),
+         (W.TRIANGLE_MIRRORED, 6), (W.TRIANGLE, 0), (W.TRIANGLE, 1), (W.MENGER, 1)]
+
+
+# --------------------------------------------------------------------- maps
+
+@pytest.mark.parametrize("fam,r", SMALL)
+def test_maps_exhaustive(P, fam, r):
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    w = torch.arange(g.cells, dtype=torch.int64, device="cuda")
+    lam = g.lam(w).cpu().numpy()
+    assert np.array_equal(lam, o.lam(np.arange(g.cells)))
+    c = all_coords(g.side, fam.dim, margin=2)
+    ct = torch.from_numpy(c.astype(np.int32)).cuda()
+    assert np.array_equal(g.nu(ct).cpu().numpy(), o.nu(c))
+    assert np.array_equal(g.nu2d(ct).cpu().numpy(), o.nu2d(c))
+
+
+def test_lambda_out_of_range(P):
+    g = gpu_fr(P, W.TRIANGLE, 5)
+    w = torch.tensor([-1, g.cells, g.cells - 1], dtype=torch.int64, device="cuda")
+    out = g.lam(w).cpu().numpy()
+    assert (out[:2] == -1).all() and (out[2] >= 0).all()
+
+
+FULL = [(W.TRIANGLE, 16), (W.TRIANGLE, 20), (W.CARPET, 10), (W.VICSEK, 12), (W.MENGER, 6)]
+
+
+def boundary_omegas(k, r):
+    out = [0, k ** r - 1]
+    for mu in range(r):
+        for j in range(1, k):
+            out.append(j * k ** mu)
+            out.append(k ** r - 1 - j * k ** mu)
+    return np.unique(np.array(out, dtype=np.int64))
+
+
+@pytest.mark.parametrize("fam,r", FULL)
+def test_maps_sampled_full_size(P, fam, r):
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    w = np.concatenate([boundary_omegas(fam.k, r), W.sample_omegas(g.cells, 200_000, 101 + r)])
+    lam = g.lam(torch.from_numpy(w).cuda()).cpu().numpy()
+    ref = o.lam(w)
+    assert np.array_equal(lam, ref)
+    c = np.concatenate([ref, W.sample_coords(g.side, fam.dim, 200_000, 202 + r, margin=1)])
+    ct = torch.from_numpy(c.astype(np.int32)).cuda()
+    assert np.array_equal(g.nu(ct).cpu().numpy(), o.nu(c))
+    assert np.array_equal(g.nu2d(ct).cpu().numpy(), o.nu2d(c))
+
+
+# -------------------------------------------------------------------- init
+
+@pytest.mark.parametrize("p", [0.0, 0.3, 0.5, 1.0])
+def test_init_bernoulli(P, p):
+    g, o = gpu_fr(P, W.CARPET, 5), ora(W.CARPET, 5)
+    # offset views exercise the unaligned head/tail of the vectorised writer
+    buf = torch.zeros(g.cells + 7, dtype=torch.uint8, device="cuda")
+    for off in (0, 3):
+        st = buf[off:off + g.cells]
+        g.init_bernoulli(99, p, out=st)
+        assert np.array_equal(st.cpu().numpy(), o.init_bernoulli(99, p))
+
+
+def test_init_full_size_sampled(P):
+    inst = W.TRI_R20
+    g = gpu_fr(P, inst.family, inst.r)
+    st = g.init_bernoulli(inst.seed, inst.p)
+    o = ora(inst.family, inst.r)
+    ref = np.zeros(g.cells, dtype=np.uint8)
+    n = 4_000_000
+    o.init_bernoulli(inst.seed, inst.p, 0, n, out=ref)
+    o.init_bernoulli(inst.seed, inst.p, g.cells - n, g.cells, out=ref)
+    assert np.array_equal(st[:n].cpu().numpy(), ref[:n])
+    assert np.array_equal(st[-n:].cpu().numpy(), ref[-n:])
+    del st
+    torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------- steps
+
+@pytest.mark.parametrize("fam,r,levels", [
+    (W.TRIANGLE, 6, [0, 1, 2, 3, 5, 6]), (W.CARPET, 4, [0, 1, 2, 3, 4]),
+    (W.VICSEK, 5, [0, 2, 4, 5]), (W.MENGER, 3, [0, 1, 2, 3]), (W.FULL_SQUARE, 5, [0, 2, 5]),
+    (W.TRIANGLE_MIRRORED, 7, [3, 7]), (W.TRIANGLE, 0, [0]), (W.MENGER, 1, [0, 1])])
+def test_step_exhaustive_all_tile_depths(P, fam, r, levels):
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(1000 + r, 0.45)
+    ref = o.step(init, rule=oracle_rule(fam), steps=3)
+    x = torch.from_numpy(init).cuda()
+    for L in levels:
+        g.tile_levels = L
+        assert g.tile_levels == L
+        out = g.step(x, steps=3, rule=rule_of(fam))
+        assert np.array_equal(out.cpu().numpy(), ref), f"L={L}"
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2, 3, 4])
+def test_step_ping_pong_counts(P, steps):
+    fam, r = W.VICSEK, 5
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    rng = np.random.default_rng(steps)
+    raw = rng.integers(0, 256, size=g.cells).astype(np.uint8)  # nonzero bytes are alive
+    x = torch.from_numpy(raw).cuda()
+    out = g.step(x, steps=steps)
+    assert np.array_equal(out.cpu().numpy(), o.step(raw, steps=steps))
+    assert np.array_equal(x.cpu().numpy(), raw)  # input never written
+
+
+def test_config1_triangle_r8_compact_and_bb(P):
+    inst = W.TRI_R8
+    fam, r = inst.family, inst.r
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    st = g.init_bernoulli(inst.seed, inst.p)
+    init = o.init_bernoulli(inst.seed, inst.p)
+    assert np.array_equal(st.cpu().numpy(), init)
+    ref = o.step(init, steps=inst.steps)
+    out = g.step(st, steps=inst.steps)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    box = g.scatter(st)
+    assert np.array_equal(box.cpu().numpy(), o.scatter(init))
+    bb = g.bb_step(box, steps=inst.steps)
+    ref_box = o.bb_step(o.scatter(init), steps=inst.steps)
+    assert np.array_equal(bb.cpu().numpy(), ref_box)
+    assert np.array_equal(g.gather(bb).cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("fam,r", [(W.TRIANGLE, 6), (W.CARPET, 3), (W.VICSEK, 4), (W.MENGER, 2),
+                                   (W.TRIANGLE, 0), (W.FULL_SQUARE, 4)])
+def test_bb_exhaustive_with_garbage(P, fam, r):
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    rng = np.random.default_rng(r + 7)
+    box = rng.integers(0, 4, size=g.box_cells).astype(np.uint8)  # garbage off the fractal too
+    b = torch.from_numpy(box).cuda()
+    for steps in (0, 1, 2, 5):
+        out = g.bb_step(b, steps=steps, rule=rule_of(fam))
+        assert np.array_equal(out.cpu().numpy(), o.bb_step(box, rule=oracle_rule(fam), steps=steps))
+
+
+def test_scatter_gather_roundtrip(P):
+    for fam, r in [(W.CARPET, 4), (W.MENGER, 3), (W.TRIANGLE, 9)]:
+        g, o = gpu_fr(P, fam, r), ora(fam, r)
+        init = o.init_bernoulli(5, 0.5)
+        x = torch.from_numpy(init).cuda()
+        box = g.scatter(x)
+        assert np.array_equal(box.cpu().numpy(), o.scatter(init))
+        assert np.array_equal(g.gather(box).cpu().numpy(), o.gather(o.scatter(init)))
+
+
+def test_run_host_matches_device(P):
+    fam, r = W.TRIANGLE, 9
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(77, 0.4)
+    hin = torch.from_numpy(init).pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    g.run_host(hin, hout, steps=7)
+    assert np.array_equal(hout.numpy(), o.step(init, steps=7))
+
+
+# ---------------------------------------------------- full-size, sampled
+
+def _full_size_check(P, inst, samples, gens=(1, 2)):
+    fam, r = inst.family, inst.r
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(inst.seed, inst.p)           # oracle's own input
+    st = g.init_bernoulli(inst.seed, inst.p)             # the library's input
+    w = np.concatenate([boundary_omegas(fam.k, r), W.sample_omegas(g.cells, samples, 7 + r)])
+    wt = torch.from_numpy(w).cuda()
+    assert np.array_equal(st[wt].cpu().numpy(), init[w])
+    a = st
+    b = torch.empty_like(st)
+    done = 0
+    for t in sorted(gens):
+        while done < t:
+            g.step(a, out=b, steps=1, rule=rule_of(fam))
+            a, b = b, a
+            done += 1
+        ref = o.cells_after(init, w, t, rule=oracle_rule(fam))
+        assert np.array_equal(a[wt].cpu().numpy(), ref), f"generation {t}"
+    del a, b, st
+    torch.cuda.empty_cache()
+
+
+def test_full_size_triangle_r20(P):
+    _full_size_check(P, W.TRI_R20, 20_000, gens=(1, 2))
+
+
+def test_full_size_triangle_r16_full_generation(P):
+    inst = W.TRI_R16
+    g, o = gpu_fr(P, inst.family, inst.r), ora(inst.family, inst.r)
+    init = o.init_bernoulli(inst.seed, inst.p)
+    st = g.init_bernoulli(inst.seed, inst.p)
+    out = g.step(st, steps=1)
+    assert np.array_equal(out.cpu().numpy(), o.step(init, steps=1))
+    _full_size_check(P, inst, 20_000, gens=(3,))
+
+
+@pytest.mark.parametrize("inst", [W.CARPET_R10, W.VICSEK_R12, W.MENGER_R6], ids=lambda i: i.family.name)
+def test_full_size_other_fractals(P, inst):
+    _full_size_check(P, inst, 10_000, gens=(1, 2))
+
+
+def test_full_size_bb_triangle_r16(P):
+    inst = W.TRI_R16
+    fam, r = inst.family, inst.r
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(inst.seed, inst.p)
+    st = g.init_bernoulli(inst.seed, inst.p)
+    box = g.scatter(st)
+    out = g.bb_step(box, steps=1)
+    del box
+    ref = o.step(init, steps=1)
+    # sampled box cells: members must equal the compact oracle, the rest 0
+    c = np.concatenate([o.lam(W.sample_omegas(g.cells, 50_000, 3)),
+                        W.sample_coords(g.side, 2, 50_000, 4)])
+    idx = c[:, 0] + g.side * c[:, 1]
+    nu = o.nu(c)
+    expect = np.where(nu >= 0, ref[np.maximum(nu, 0)], 0).astype(np.uint8)
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(got, expect)
+    # and the whole box gathers back to the oracle's compact generation
+    assert np.array_equal(g.gather(out).cpu().numpy(), ref)
+    del out
+    torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------ error paths
+
+def test_errors(P):
+    from paper_2110_12952_gb300.capi import FractalError
+    with pytest.raises(FractalError, match="EINVAL"):
+        P.Fractal(3, 2, 4, 2, [[0, 0], [1, 0], [1, 0]])  # duplicate rows
+    with pytest.raises(FractalError, match="EINVAL"):
+        P.Fractal(3, 2, 4, 2, [[0, 0], [1, 0], [2, 0]])  # outside [0,s)
+    with pytest.raises(FractalError, match="EINVAL"):
+        P.Fractal(5, 2, 4, 2, [[0, 0], [1, 0], [0, 1], [1, 1], [0, 0]])  # k > s^dim
+    with pytest.raises(FractalError, match="EOVERFLOW"):
+        P.Fractal(3, 2, 31, 2, W.TRIANGLE.table())  # s^r >= 2^31
+    g = gpu_fr(P, W.TRIANGLE, 6)
+    x = torch.zeros(g.cells * 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(FractalError, match="EINVAL"):
+        g.step(x[: g.cells], out=x[5: 5 + g.cells])  # overlapping buffers
+    with pytest.raises(FractalError, match="EINVAL"):
+        g.step(x[: g.cells], out=x[g.cells:], steps=-1)
+    with pytest.raises(FractalError, match="EINVAL"):
+        g.tile_levels = 7
