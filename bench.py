@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-bb", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tile-levels", type=int, default=-1, help="tile depth L (-1: library choice)")
     return ap.parse_args()
 
 
@@ -245,6 +246,8 @@ def run_ours(args, rank, world, dist):
     inst = W.TRI_R20 if args.r == 20 else W.Instance(W.TRIANGLE, args.r, 0.3, 3, 1000)
     fam = inst.family
     g = Fractal.from_family(fam, inst.r)
+    if args.tile_levels >= 0:
+        g.tile_levels = args.tile_levels
     a = g.init_bernoulli(inst.seed + rank, inst.p)
     b = torch.empty_like(a)
     bufs = [a, b]
@@ -288,7 +291,7 @@ def run_ours(args, rank, world, dist):
     achieved = alg_bytes / (ms / args.steps / 1e3) / 1e9
     workload = workload_config(inst)["workload"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_per_launch(workload), "kernel": "step_tiled_kernel<2>",
+            "traffic": traffic_per_launch(workload), "kernel": "step_tma_kernel<2,4>",
             "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src,
             "tile_levels": g.tile_levels}
 

@@ -87,8 +87,7 @@ int fractal_destroy(fractal_t *f);
 int fractal_info(const fractal_t *f, int64_t *cells, int64_t *side);
 
 /* lambda (Sec. 3): coords_dev[e*dim + i] = axis i of lambda(omega_dev[e]),
- * for e < count.  Every omega must be in [0, k^r); others give FR_EINVAL at
- * the next call (their coordinates are written as -1). */
+ * for e < count.  An omega outside [0, k^r) gets the coordinates -1. */
 int fractal_lambda(const fractal_t *f, const int64_t *omega_dev, int64_t count,
                    int32_t *coords_dev, void *stream);
 
@@ -156,6 +155,11 @@ int fractal_get_tile_levels(const fractal_t *f, int *levels);
 
 /* Waits for `stream` and reports any asynchronous CUDA error. */
 int fractal_sync(void *stream);
+
+/* Waits for the device, then returns FR_ETIMEOUT if a kernel of this handle
+ * gave up a bounded device-side wait since the last check (the outputs of
+ * that call are then invalid), FR_OK otherwise.  Clears the flag. */
+int fractal_check(fractal_t *f);
 
 #ifdef __cplusplus
 }

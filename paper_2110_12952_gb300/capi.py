@@ -49,6 +49,7 @@ SIGNATURES = {
     "fractal_set_tile_levels": (c_int, [c_fp, c_int]),
     "fractal_get_tile_levels": (c_int, [c_fp, ctypes.POINTER(c_int)]),
     "fractal_sync": (c_int, [c_vp]),
+    "fractal_check": (c_int, [c_fp]),
 }
 
 

@@ -45,6 +45,28 @@ static bool mul_ok(int64_t a, int64_t b, int64_t limit, int64_t *out)
 
 int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st);
 
+int ensure_status(fractal *f)
+{
+    if (f->status) return FR_OK;
+    FR_CUDA(cudaMalloc(&f->status, sizeof(int)));
+    FR_CUDA(cudaMemset(f->status, 0, sizeof(int)));
+    return FR_OK;
+}
+
+// Reads and clears the device status word (call after the work finished).
+int take_status(fractal *f)
+{
+    if (!f->status) return FR_OK;
+    int v = 0;
+    FR_CUDA(cudaMemcpy(&v, f->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        FR_CUDA(cudaMemset(f->status, 0, sizeof(int)));
+        set_error(v, "a bounded device-side wait gave up; the results of that call are invalid");
+        return v;
+    }
+    return FR_OK;
+}
+
 }  // namespace fr
 
 using namespace fr;
@@ -129,6 +151,7 @@ extern "C" int fractal_destroy(fractal_t *f)
     cudaFree(f->bb_scratch);
     cudaFree(f->host_io[0]);
     cudaFree(f->host_io[1]);
+    cudaFree(f->status);
     delete f;
     return FR_OK;
 }
@@ -259,7 +282,7 @@ extern "C" int fractal_run_host(fractal_t *f, const uint8_t *host_in, uint8_t *h
     if (rc) return rc;
     FR_CUDA(cudaMemcpyAsync(host_out, f->host_io[1], (size_t)f->cells, cudaMemcpyDeviceToHost, st));
     FR_CUDA(cudaStreamSynchronize(st));
-    return FR_OK;
+    return take_status(f);
 }
 
 extern "C" int fractal_sync(void *stream)
@@ -268,4 +291,12 @@ extern "C" int fractal_sync(void *stream)
     FR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     FR_CUDA(cudaGetLastError());
     return FR_OK;
+}
+
+extern "C" int fractal_check(fractal_t *f)
+{
+    g_err.clear();
+    if (!f) return fail(FR_EINVAL, "fractal_check: handle is NULL");
+    FR_CUDA(cudaDeviceSynchronize());
+    return take_status(f);
 }

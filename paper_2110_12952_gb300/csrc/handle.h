@@ -26,10 +26,23 @@ struct StepPlan {
     int coarse_levels = 0; // r - L
     int nring = 0;         // halo cells to fetch per tile
     uint32_t *pos = nullptr;   // [KL] box offset of local cell l
-    uint32_t *ring = nullptr;  // [2*nring] (box offset | dir << 24, local omega)
+    uint32_t *ring = nullptr;  // [2*nring] (box offset | slot << 24, local omega)
+    int32_t *nbr = nullptr;    // [NT][nbrw] compact index of each neighbour tile, -1 = none
+    int nbrw = 0;          // int32 entries per table row (3^dim - 1, padded to 16 B)
+    int nstage = 0;        // input pipeline depth
+    int stage_bytes = 0;   // one input stage: table row + tile bytes
+    int tile_bytes = 0;    // 16-aligned superset of a tile
+    int off_bar = 0, off_box = 0, off_pos = 0, off_out = 0;  // shared-memory layout
     int smem = 0;          // dynamic shared memory per CTA
     int block = 256;
     int grid = 0;
+    int mode = 0;          // 0: per-cell neighbour reads; 3 or 4: group mode, block side s^G
+    int G = 0;             // levels per group (group mode)
+    int KG = 0;            // k^G cells per group
+    int Px = 0, Py = 0;    // box row pitch (bytes) and rows per plane
+    int ntab = 0;          // entries of the per-tile table (cells or groups)
+    int8_t lid_of_q[16] = {};    // block position -> cell of the group, -1 = none
+    int16_t rel_of_lid[16] = {}; // cell of the group -> offset from the window base
 };
 
 // Bounding-box step (Sec. 4 "BB"): membership of a box cell is decided from
@@ -60,6 +73,7 @@ struct fractal {
     uint8_t *scratch = nullptr;      // k^r bytes, ping-pong for steps > 1
     uint8_t *bb_scratch = nullptr;   // n^dim bytes, ping-pong for BB steps > 1
     uint8_t *host_io[2] = {nullptr, nullptr};  // device buffers of run_host
+    int *status = nullptr;           // device word set by kernels whose bounded waits gave up
 };
 
 namespace fr {
@@ -74,5 +88,7 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
 int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                    uint32_t survive, cudaStream_t st);
 int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st);
+int ensure_status(fractal *f);
+int take_status(fractal *f);
 
 }  // namespace fr

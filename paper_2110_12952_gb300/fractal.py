@@ -161,3 +161,7 @@ class Fractal:
 
     def sync(self, stream=None):
         self._check(self._lib.fractal_sync(_stream(stream)))
+
+    def check(self):
+        """Raise if a bounded device-side wait of this handle gave up."""
+        self._check(self._lib.fractal_check(self._h))
