@@ -246,10 +246,12 @@ def run_ours(args, rank, world, dist):
     inst = W.TRI_R20 if args.r == 20 else W.Instance(W.TRIANGLE, args.r, 0.3, 3, 1000)
     fam = inst.family
     g = Fractal.from_family(fam, inst.r)
-    if args.tile_levels >= 0:
-        g.tile_levels = args.tile_levels
     a = g.init_bernoulli(inst.seed + rank, inst.p)
     b = torch.empty_like(a)
+    if args.tile_levels >= 0:
+        g.tile_levels = args.tile_levels
+    else:
+        g.autotune(a, b)   # picks the tile depth; untimed
     bufs = [a, b]
     cur = [0]
 
@@ -346,6 +348,7 @@ def bb_compare(args, W):
 
     st = g.init_bernoulli(inst.seed, inst.p)
     out = torch.empty_like(st)
+    g.autotune(st, out)
     n = max(5, min(args.steps, 20))
     ct = time_steps(lambda: g.step(st, out=out, steps=1), n, 3, flush=flush)
     box = g.scatter(st)

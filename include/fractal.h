@@ -153,6 +153,16 @@ int fractal_run_host(fractal_t *f, const uint8_t *host_in, uint8_t *host_out,
 int fractal_set_tile_levels(fractal_t *f, int levels);
 int fractal_get_tile_levels(const fractal_t *f, int *levels);
 
+/* Autotuner of fractal_step: times one generation from in_dev into out_dev
+ * (both k^r bytes; out_dev is overwritten) for each candidate tile depth
+ * (the deepest whose shared-memory layout fits, and the three below), keeps
+ * the fastest for this handle and remembers it for every later handle of the
+ * same fractal and level on the same GPU model in this process.  Waits for
+ * `stream`.  *levels (if not NULL) receives the chosen depth. */
+int fractal_autotune(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
+                     uint32_t birth_mask, uint32_t survive_mask, void *stream,
+                     int *levels);
+
 /* Waits for `stream` and reports any asynchronous CUDA error. */
 int fractal_sync(void *stream);
 

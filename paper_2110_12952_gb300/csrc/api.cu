@@ -136,6 +136,7 @@ extern "C" int fractal_create(int k, int s, int r, int dim, const int32_t *offse
         delete f;
         return cuda_fail(e, "fractal_create: no usable CUDA device");
     }
+    f->tile_levels_user = cached_tile_levels(f);
     *out = f;
     return FR_OK;
 }
@@ -299,4 +300,13 @@ extern "C" int fractal_check(fractal_t *f)
     if (!f) return fail(FR_EINVAL, "fractal_check: handle is NULL");
     FR_CUDA(cudaDeviceSynchronize());
     return take_status(f);
+}
+
+extern "C" int fractal_autotune(fractal_t *f, const uint8_t *in, uint8_t *out, uint32_t birth,
+                                uint32_t survive, void *stream, int *levels)
+{
+    g_err.clear();
+    if (!f || !in || !out) return fail(FR_EINVAL, "fractal_autotune: NULL argument");
+    if (overlap(in, out, f->cells)) return fail(FR_EINVAL, "fractal_autotune: in and out overlap");
+    return autotune_step(f, in, out, birth, survive, (cudaStream_t)stream, levels);
 }

@@ -43,6 +43,9 @@ struct StepPlan {
     int ntab = 0;          // entries of the per-tile table (cells or groups)
     int8_t lid_of_q[16] = {};    // block position -> cell of the group, -1 = none
     int16_t rel_of_lid[16] = {}; // cell of the group -> offset from the window base
+    int xoff = 0;                // box byte of padded column 0 (3 in quad mode)
+    uint32_t row_sel[8] = {};    // quad mode: byte selectors, group cells -> block rows
+    uint32_t pack_sel[9] = {};   // quad mode: byte selectors, block sums -> cell order
 };
 
 // Bounding-box step (Sec. 4 "BB"): membership of a box cell is decided from
@@ -90,5 +93,8 @@ int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
 int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st);
 int ensure_status(fractal *f);
 int take_status(fractal *f);
+int cached_tile_levels(const fractal *f);
+int autotune_step(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth, uint32_t survive,
+                  cudaStream_t st, int *best);
 
 }  // namespace fr

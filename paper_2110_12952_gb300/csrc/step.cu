@@ -21,21 +21,31 @@
 //     written back with bulk stores; the at most 15 unaligned bytes at each
 //     end of a tile are written with plain stores.
 //   * The tile's cells are scattered into a shared-memory box with a one-cell
-//     halo.  Cells of the box that are not local members stay 0 forever; halo
-//     cells that are members and touch a member of the tile (list `ring`) are
+//     halo.  Cells of the box that are not local members stay 0; halo cells
+//     that are members and touch a member of the tile (list `ring`) are
 //     fetched from the neighbouring tiles.
-//   * Neighbour counts, 2D "group" mode: one thread owns a level-G subtree
-//     (k^G cells, contiguous in omega, filling an s^G x s^G block with
-//     s^G = 3 or 4).  It loads the (s^G+2)-wide window rows of its block as
-//     32-bit words and adds them byte-wise (a byte holds a count <= 9, so no
-//     carries cross bytes): three row adds give vertical sums, two funnel
-//     shifts and adds give the 3x3 sums of a whole block row at once.
-//     Other cases ("cell" mode, 3D or other s) read the 3^dim - 1 neighbour
-//     bytes of each cell from the box.
+//
+// Three ways to count neighbours from the box (the "policy" of the kernel):
+//   * quad (2D, s = 2, k = 3): a level-2 group is 9 cells, contiguous in
+//     omega, filling a 4x4 block.  A thread owns 4 consecutive groups (36
+//     bytes = 9 aligned words of input and of output).  Box rows of a block
+//     are assembled with byte permutes and stored as words; the 6x6 window of
+//     a block is added byte-wise (a byte holds a count <= 9, so no carry
+//     crosses a byte): three row adds give vertical sums, two funnel shifts
+//     and two adds give the 3x3 sums of a block row.  The sums are permuted
+//     back into omega order and the rule is applied to 4 cells at a time as a
+//     byte look-up (prmt).
+//   * group (2D, s^G = 3 or 4): the same window sums per group, one thread
+//     per group, byte stores.
+//   * cell (any other case, 3D): each cell reads its 3^dim - 1 neighbours.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "handle.h"
@@ -44,6 +54,8 @@
 namespace fr {
 
 constexpr int kMaxGroup = 16;  // cells per group / block positions (s^G <= 4)
+constexpr int kQuadKG = 9;     // cells per group in quad mode
+constexpr int kRingRegs = 4;   // halo values per thread prefetched in registers
 
 struct StepArgs {
     int64_t KL, NT, cells;
@@ -51,14 +63,17 @@ struct StepArgs {
     int nring, nbrw, nstage, stage_bytes, tile_bytes;
     int off_bar, off_box, off_tab, off_out, box_bytes;
     int ntab;              // entries of the shared table (cells or groups)
-    int KG;                // cells per group (group mode)
-    const uint32_t *tab;   // cell mode: box offset per cell; group mode: window base per group
+    int KG;                // cells per group (group / quad mode)
+    const uint32_t *tab;   // cell mode: box offset per cell; else window base per group
     const uint32_t *ring;
     const int32_t *nbr;
     uint32_t birth, survive;
+    uint32_t lut[4];       // quad mode: rule as byte tables (dead lo/hi, live lo/hi)
     int *status;
-    int8_t lid_of_q[kMaxGroup];     // group mode: block position -> cell of the group, -1 none
-    int16_t rel_of_lid[kMaxGroup];  // group mode: cell of the group -> offset from window base
+    int8_t lid_of_q[kMaxGroup];     // block position -> cell of the group, -1 none
+    int16_t rel_of_lid[kMaxGroup];  // cell of the group -> box offset from the window base
+    uint32_t row_sel[8];            // quad: cells -> block row j (two selectors per row)
+    uint32_t pack_sel[9];           // quad: block sums -> cell order (three per word)
 };
 
 // --------------------------------------------------------------- host plan
@@ -117,29 +132,46 @@ static int group_levels(const fractal *f)
     return 0;
 }
 
+enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9 };
+
 struct Geometry {
-    int mode;       // 0 = cell, 3 or 4 = group block side
-    int G;          // levels per group
+    int mode, G, xoff;
     int64_t B, Px, Py, planes;
-    int64_t box_bytes, tab_entries;
+    int64_t box_bytes, tab_entries, block;
 };
+
+static int64_t odd_words(int64_t px)
+{
+    px = (px + 3) / 4 * 4;
+    if ((px / 4) % 2 == 0) px += 4;  // pitch/4 odd spreads block rows over banks
+    return px;
+}
 
 static Geometry plan_geometry(const fractal *f, int L)
 {
     Geometry g;
     g.B = ipow(f->s, L);
     g.G = group_levels(f);
-    g.mode = (g.G > 0 && L >= g.G && ipow(f->k, g.G) <= kMaxGroup) ? (int)ipow(f->s, g.G) : 0;
-    if (!g.mode) g.G = 0;
-    if (g.mode) {
-        // rows padded so window words never run past a row; pitch/4 odd
-        // spreads the rows of neighbouring blocks over the banks
-        g.Px = (g.B + 4 + 3) / 4 * 4;
-        if ((g.Px / 4) % 2 == 0) g.Px += 4;
+    g.xoff = 0;
+    g.block = 256;
+    const bool grp = g.G > 0 && L >= g.G && ipow(f->k, g.G) <= kMaxGroup;
+    if (grp) {
+        g.mode = (int)ipow(f->s, g.G);
+        g.tab_entries = ipow(f->k, L - g.G);
         g.Py = g.B + 2;
         g.planes = 1;
-        g.tab_entries = ipow(f->k, L - g.G);
+        const int64_t units = (g.tab_entries + 3) / 4 + 1;
+        if (g.mode == 4 && ipow(f->k, g.G) == kQuadKG && units <= 256) {
+            g.mode = kModeQuad;
+            g.xoff = 3;
+            g.Px = odd_words(g.B + 8);
+            g.block = std::max<int64_t>(64, (units + 31) / 32 * 32);  // one unit per thread
+        } else {
+            g.Px = odd_words(g.B + 4);
+        }
     } else {
+        g.mode = kModeCell;
+        g.G = 0;
         g.Px = g.B + 2;
         g.Py = g.B + 2;
         g.planes = (f->dim == 3) ? g.B + 2 : 1;
@@ -149,8 +181,14 @@ static Geometry plan_geometry(const fractal *f, int L)
     return g;
 }
 
+// Shared memory, in order: `nstage` input stages (table row, front pad,
+// tile bytes), their mbarriers, the box, the per-tile table, and the output
+// stage (front pad, tile bytes).  The pads give the quad policy room for the
+// partial units at both ends of a tile.
+constexpr int kStagePad = 48;
+
 struct Layout {
-    int64_t stage_bytes, tile_bytes, off_bar, off_box, box_bytes, off_tab, off_out, total;
+    int64_t nstage, stage_bytes, tile_bytes, off_bar, off_box, box_bytes, off_tab, off_out, total;
 };
 
 static Layout plan_layout(const fractal *f, int L)
@@ -158,11 +196,12 @@ static Layout plan_layout(const fractal *f, int L)
     Layout y;
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
-    y.tile_bytes = round16(KL + 32);
-    y.stage_bytes = 4 * nbr_width(f->dim) + y.tile_bytes;
-    int64_t off = (int64_t)nstages() * y.stage_bytes;
+    y.nstage = (g.mode == kModeQuad) ? 2 : nstages();
+    y.tile_bytes = round16(KL + 64);
+    y.stage_bytes = 4 * nbr_width(f->dim) + kStagePad + y.tile_bytes;
+    int64_t off = y.nstage * y.stage_bytes;
     y.off_bar = off;
-    off += 8 * nstages();
+    off += 8 * y.nstage;
     off = round16(off);
     y.off_box = off;
     y.box_bytes = g.box_bytes;
@@ -170,7 +209,7 @@ static Layout plan_layout(const fractal *f, int L)
     y.off_tab = off;
     off += round16(4 * g.tab_entries);
     y.off_out = off;
-    off += y.tile_bytes;
+    off += kStagePad + y.tile_bytes;
     y.total = off;
     return y;
 }
@@ -223,16 +262,16 @@ __global__ void nbr_table_kernel(FracDev F, int64_t NT, int coarse_levels, int32
     }
 }
 
-template <int DIM, int SG>
+template <int DIM, int MODE>
 __global__ void step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in,
                                 uint8_t *__restrict__ out);
 
-template <int DIM, int SG>
+template <int DIM, int MODE>
 static int configure(StepPlan &p, int num_sms)
 {
     int per_sm = 0;
-    FR_CUDA(cudaFuncSetAttribute(step_tma_kernel<DIM, SG>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
-    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tma_kernel<DIM, SG>, p.block, p.smem));
+    FR_CUDA(cudaFuncSetAttribute(step_tma_kernel<DIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
+    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tma_kernel<DIM, MODE>, p.block, p.smem));
     if (per_sm < 1) {
         set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
         return FR_EINVAL;
@@ -240,6 +279,9 @@ static int configure(StepPlan &p, int num_sms)
     p.grid = (int)std::min<int64_t>((int64_t)per_sm * num_sms, p.NT);
     return FR_OK;
 }
+
+// Selector nibble that yields a zero byte (sign of a byte whose msb is 0).
+static constexpr uint32_t kZeroSel = 0x8;
 
 int ensure_step_plan(fractal *f)
 {
@@ -265,6 +307,7 @@ int ensure_step_plan(fractal *f)
     p.Px = (int)geo.Px;
     p.Py = (int)geo.Py;
     p.P = p.Px;
+    p.xoff = geo.xoff;
     p.box_bytes = (int)y.box_bytes;
     p.stage_bytes = (int)y.stage_bytes;
     p.tile_bytes = (int)y.tile_bytes;
@@ -273,13 +316,14 @@ int ensure_step_plan(fractal *f)
     p.off_pos = (int)y.off_tab;
     p.off_out = (int)y.off_out;
     p.smem = (int)y.total;
-    p.nstage = nstages();
+    p.nstage = (int)y.nstage;
     p.nbrw = nbr_width(f->dim);
     p.ntab = (int)geo.tab_entries;
+    p.block = (int)geo.block;
     const int dim = f->dim;
     const int64_t W[3] = {geo.B + 2, geo.B + 2, dim == 3 ? geo.B + 2 : 1};  // padded extents
     auto offset_of = [&](const int b[3]) -> int64_t {
-        return b[0] + geo.Px * (b[1] + geo.Py * (int64_t)(dim == 3 ? b[2] : 0));
+        return (b[0] + geo.xoff) + geo.Px * (b[1] + geo.Py * (int64_t)(dim == 3 ? b[2] : 0));
     };
     if (geo.Px * geo.Py * geo.planes >= (1 << 24)) {
         set_error(FR_EINVAL, "fractal_step: tile box too large");
@@ -288,7 +332,7 @@ int ensure_step_plan(fractal *f)
 
     // local lambda -> padded box offset; occupancy of the interior
     std::vector<uint32_t> pos(p.KL);
-    std::vector<uint8_t> occ((size_t)(geo.Px * geo.Py * geo.planes), 0);
+    std::vector<uint8_t> occ((size_t)(geo.Px * geo.Py * geo.planes + 16), 0);
     for (int64_t l = 0; l < p.KL; ++l) {
         int c[3];
         host_lambda(f, l, L, c);
@@ -298,23 +342,60 @@ int ensure_step_plan(fractal *f)
         occ[o] = 1;
     }
     std::vector<uint32_t> tab;
-    if (p.mode) {
+    if (p.mode != kModeCell) {
         // group g = cells [g k^G, (g+1) k^G); its block sits at s^G * (coarse
         // lambda of g over L - G levels); the window starts one cell up-left
-        const int KG = (int)ipow(f->k, p.G), SG = p.mode;
+        const int KG = (int)ipow(f->k, p.G), SG = (int)ipow(f->s, p.G);
         p.KG = KG;
         for (int q = 0; q < kMaxGroup; ++q) p.lid_of_q[q] = -1;
         for (int lid = 0; lid < KG; ++lid) {
             int c[3];
             host_lambda(f, lid, p.G, c);
             p.lid_of_q[c[1] * SG + c[0]] = (int8_t)lid;
-            p.rel_of_lid[lid] = (int16_t)((c[1] + 1) * geo.Px + (c[0] + 1));
+            p.rel_of_lid[lid] = (int16_t)((c[1] + 1) * geo.Px + (c[0] + 1) + geo.xoff);
         }
         tab.resize(geo.tab_entries);
         for (int64_t g = 0; g < geo.tab_entries; ++g) {
             int c[3];
             host_lambda(f, g, L - p.G, c);
             tab[g] = (uint32_t)((int64_t)c[1] * SG * geo.Px + (int64_t)c[0] * SG);
+        }
+        if (p.mode == kModeQuad) {
+            // block row j <- group cells: first permute over words 0,1 of the
+            // group, then take cells 8..11 from word 2
+            for (int j = 0; j < 4; ++j) {
+                uint32_t sa = 0, sb = 0;
+                for (int c = 0; c < 4; ++c) {
+                    const int lid = p.lid_of_q[j * 4 + c];
+                    const uint32_t na = (lid >= 0 && lid < 8) ? (uint32_t)lid : kZeroSel;
+                    const uint32_t nb = (lid >= 8) ? (uint32_t)(4 + lid - 8) : (uint32_t)c;
+                    sa |= na << (4 * c);
+                    sb |= nb << (4 * c);
+                }
+                p.row_sel[2 * j] = sa;
+                p.row_sel[2 * j + 1] = sb;
+            }
+            // cell order word m <- block sums (16 bytes: row j, column c at 4j+c)
+            for (int m = 0; m < 3; ++m) {
+                uint32_t sa = 0, sb = 0, sc = 0;
+                for (int i = 0; i < 4; ++i) {
+                    const int lid = 4 * m + i;
+                    uint32_t na = kZeroSel, nb = kZeroSel, nc = kZeroSel;
+                    if (lid < KG) {
+                        int c[3];
+                        host_lambda(f, lid, p.G, c);
+                        const int idx = 4 * c[1] + c[0];
+                        if (idx < 8) { na = idx; nc = i; }
+                        else { nb = idx - 8; nc = 4 + i; }
+                    }
+                    sa |= na << (4 * i);
+                    sb |= nb << (4 * i);
+                    sc |= nc << (4 * i);
+                }
+                p.pack_sel[3 * m] = sa;
+                p.pack_sel[3 * m + 1] = sb;
+                p.pack_sel[3 * m + 2] = sc;
+            }
         }
     } else {
         tab = pos;
@@ -376,11 +457,11 @@ int ensure_step_plan(fractal *f)
         FR_CUDA(cudaGetLastError());
         FR_CUDA(cudaDeviceSynchronize());
     }
-    p.block = 256;
-    if (dim == 3) rc = configure<3, 0>(p, f->num_sms);
-    else if (p.mode == 4) rc = configure<2, 4>(p, f->num_sms);
-    else if (p.mode == 3) rc = configure<2, 3>(p, f->num_sms);
-    else rc = configure<2, 0>(p, f->num_sms);
+    if (dim == 3) rc = configure<3, kModeCell>(p, f->num_sms);
+    else if (p.mode == kModeQuad) rc = configure<2, kModeQuad>(p, f->num_sms);
+    else if (p.mode == kModeGroup4) rc = configure<2, kModeGroup4>(p, f->num_sms);
+    else if (p.mode == kModeGroup3) rc = configure<2, kModeGroup3>(p, f->num_sms);
+    else rc = configure<2, kModeCell>(p, f->num_sms);
     if (rc) {
         free_step_plan(p);
         return rc;
@@ -389,49 +470,68 @@ int ensure_step_plan(fractal *f)
     return FR_OK;
 }
 
-// ------------------------------------------------------------------ kernel
-
-// Issue the bulk loads of tile T into one stage: the table row and the
-// 16-byte-aligned part of the tile's bytes that lies inside the buffer.
-__device__ __forceinline__ void issue_tile(const StepArgs &a, const uint8_t *in, int64_t T,
-                                           uint8_t *stage, uint64_t *bar)
-{
-    const uintptr_t start = (uintptr_t)(in + T * a.KL);
-    const uintptr_t end = start + (uintptr_t)a.KL;
-    const uintptr_t lo = start & ~(uintptr_t)15;
-    const uintptr_t in_lo = ((uintptr_t)in + 15) & ~(uintptr_t)15;
-    const uintptr_t in_hi = ((uintptr_t)in + (uintptr_t)a.cells) & ~(uintptr_t)15;
-    uintptr_t b0 = lo > in_lo ? lo : in_lo;
-    uintptr_t b1 = ((end + 15) & ~(uintptr_t)15);
-    if (b1 > in_hi) b1 = in_hi;
-    const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
-    const uint32_t data_bytes = b1 > b0 ? (uint32_t)(b1 - b0) : 0u;
-    mbar_arrive_expect_tx(bar, row_bytes + data_bytes);
-    bulk_g2s(stage, a.nbr + T * a.nbrw, row_bytes, bar);
-    if (data_bytes) bulk_g2s(stage + row_bytes + (b0 - lo), (const void *)b0, data_bytes, bar);
-}
+// ------------------------------------------------------------------ device
 
 __device__ __forceinline__ uint32_t lds32(const uint8_t *p)
 {
     return *reinterpret_cast<const uint32_t *>(p);
 }
 
-// Group mode: new states of the k^G cells of one group from its window.
-template <int SG>
-__device__ __forceinline__ void group_compute(const StepArgs &a, const uint8_t *box, uint32_t base,
-                                              uint8_t *gout)
+__device__ __forceinline__ void sts32(uint8_t *p, uint32_t v)
 {
-    constexpr int R = SG + 2;
-    uint32_t lo[R], hi[R];
+    *reinterpret_cast<uint32_t *>(p) = v;
+}
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// nonzero byte -> 1, zero byte -> 0
+__device__ __forceinline__ uint32_t bytes_to_01(uint32_t v)
+{
+    return (((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) >> 7 & 0x01010101u;
+}
+
+// Life-like rule on 4 cells at once: t = 3x3 sum including the cell (<= 9),
+// alive = 0/1 bytes.  The look-up tables hold, in byte j, the outcome for a
+// total of j in bit 0 and for a total of j + 8 in bit 7; prmt returns byte
+// (t & 7), or its bit 7 replicated when t >= 8.
+__device__ __forceinline__ uint32_t rule4(const uint32_t lut[4], uint32_t t, uint32_t alive)
+{
+    const uint32_t x = t | (t >> 4);
+    const uint32_t sel = prmt(x, 0u, 0x3120u);   // nibble i = total of cell i
+    const uint32_t rd = prmt(lut[0], lut[1], sel) & 0x01010101u;
+    const uint32_t rl = prmt(lut[2], lut[3], sel) & 0x01010101u;
+    const uint32_t m = alive * 0xffu;
+    return (rl & m) | (rd & ~m);
+}
+
+// Window of the block of one group: rows r = 0..SG+1, bytes 0..SG+1 of the
+// pair (lo, hi) are the window columns.  `ad0` is the byte address of the
+// window's first column in row 0.  Three words per row cover any alignment.
+template <int SG>
+__device__ __forceinline__ void load_window(const uint8_t *box, uint32_t ad0, int Px, uint32_t *lo,
+                                            uint32_t *hi)
+{
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t ad = base + r * a.Px;
+    for (int r = 0; r < SG + 2; ++r) {
+        const uint32_t ad = ad0 + r * Px;
         const uint32_t al = ad & ~3u;
-        const uint32_t w0 = lds32(box + al), w1 = lds32(box + al + 4);
         const uint32_t sh = (ad & 3u) * 8u;
+        const uint32_t w0 = lds32(box + al), w1 = lds32(box + al + 4), w2 = lds32(box + al + 8);
         lo[r] = __funnelshift_r(w0, w1, sh);
-        hi[r] = w1 >> sh;
+        hi[r] = __funnelshift_r(w1, w2, sh);
     }
+}
+
+// New states of the cells of one group from its window (byte stores).
+template <int SG>
+__device__ __forceinline__ void group_from_window(const StepArgs &a, const uint32_t *lo,
+                                                  const uint32_t *hi, uint8_t *gout)
+{
 #pragma unroll
     for (int j = 0; j < SG; ++j) {
         const uint32_t vl = lo[j] + lo[j + 1] + lo[j + 2];
@@ -451,16 +551,232 @@ __device__ __forceinline__ void group_compute(const StepArgs &a, const uint8_t *
     }
 }
 
-template <int DIM, int SG>
+struct TileIO {
+    const uint8_t *data;   // 16-byte aligned stage data; tile cell l at data[a_in + l]
+    uint8_t *ostage;       // 16-byte aligned output stage; tile cell l at ostage[a_out + l]
+    int a_in, a_out;
+};
+
+// ---- cell policy
+template <int DIM>
+struct CellPolicy {
+    static constexpr int NDIR = (DIM == 3) ? 27 : 9;
+    struct Regs { int nb[NDIR - 1]; };
+    __device__ static void init(const StepArgs &a, Regs &R)
+    {
+        const int PX = a.Px, PXY = a.Px * a.Py;
+        int e = 0;
+        for (int q = 0; q < NDIR; ++q) {
+            int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = (DIM == 3) ? q / 9 - 1 : 0;
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            R.nb[e++] = dx + PX * dy + PXY * dz;
+        }
+    }
+    __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *box,
+                                   const uint32_t *tab, Regs &)
+    {
+        const uint8_t *tin = io.data + io.a_in;
+        for (int64_t l = threadIdx.x; l < a.KL; l += blockDim.x) box[tab[l]] = tin[l] != 0;
+    }
+    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *box,
+                                   const uint32_t *tab, Regs &R)
+    {
+        uint8_t *tout = io.ostage + io.a_out;
+        for (int64_t l = threadIdx.x; l < a.KL; l += blockDim.x) {
+            const int p = tab[l];
+            int cnt = 0;
+#pragma unroll
+            for (int e = 0; e < NDIR - 1; ++e) cnt += box[p + R.nb[e]];
+            const uint32_t mask = box[p] ? a.survive : a.birth;
+            tout[l] = (mask >> cnt) & 1u;
+        }
+    }
+};
+
+// ---- group policy (one thread per group, byte stores)
+template <int SG>
+struct GroupPolicy {
+    struct Regs {};
+    __device__ static void init(const StepArgs &, Regs &) {}
+    __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *box,
+                                   const uint32_t *tab, Regs &)
+    {
+        const uint8_t *tin = io.data + io.a_in;
+        for (int g = threadIdx.x; g < a.ntab; g += blockDim.x) {
+            const uint32_t base = tab[g];
+            const uint8_t *src = tin + (int64_t)g * a.KG;
+            for (int lid = 0; lid < a.KG; ++lid) box[base + a.rel_of_lid[lid]] = src[lid] != 0;
+        }
+    }
+    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *box,
+                                   const uint32_t *tab, Regs &)
+    {
+        uint8_t *tout = io.ostage + io.a_out;
+        for (int g = threadIdx.x; g < a.ntab; g += blockDim.x) {
+            uint32_t lo[SG + 2], hi[SG + 2];
+            load_window<SG>(box, tab[g], a.Px, lo, hi);
+            group_from_window<SG>(a, lo, hi, tout + (int64_t)g * a.KG);
+        }
+    }
+};
+
+// ---- quad policy (s = 2, 9-cell groups, four groups per thread)
+//
+// Units of 4 consecutive groups start at group gs, the first group index
+// (possibly negative) for which the output byte offset a_out + 9 gs is a
+// multiple of 4, so every unit reads and writes whole words.  Groups of a
+// unit that lie outside [0, NG) are computed from a valid block and their
+// garbage lands in the padding before / after the tile in the stages; they
+// never touch the box.
+struct QuadPolicy {
+    static constexpr int KG = kQuadKG;
+    struct Regs {
+        uint32_t v[KG + 1];     // the unit's 36 input bytes as words (v[KG] = 0)
+        uint32_t rw[4][4];      // block rows of the four groups
+        int gq;                 // first group of the unit, or INT_MIN when idle
+    };
+    __device__ static void init(const StepArgs &, Regs &) {}
+
+    __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *box,
+                                   const uint32_t *tab, Regs &R)
+    {
+        int gs = 0;
+        while ((io.a_out + KG * gs) & 3) ++gs;
+        if (gs > 0) gs -= 4;
+        const int ng = a.ntab;
+        const int gq = gs + 4 * (int)threadIdx.x;
+        R.gq = gq < ng ? gq : INT_MIN;
+        if (R.gq == INT_MIN) return;
+        const int off = io.a_in + KG * gq;          // may be negative: stage front padding
+        const uint8_t *wp = io.data + (off & ~3);
+        const uint32_t sh = (uint32_t)(off & 3) * 8u;
+        uint32_t w[KG + 1];
+#pragma unroll
+        for (int i = 0; i <= KG; ++i) w[i] = lds32(wp + 4 * i);
+        uint32_t any = 0;
+#pragma unroll
+        for (int i = 0; i < KG; ++i) {
+            R.v[i] = __funnelshift_r(w[i], w[i + 1], sh);
+            any |= R.v[i];
+        }
+        R.v[KG] = 0;
+        if (any & 0xfefefefeu) {
+#pragma unroll
+            for (int i = 0; i < KG; ++i) R.v[i] = bytes_to_01(R.v[i]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b0 = KG * u;  // the group's 9 bytes start at byte 9u of v
+            const uint32_t g0w = __funnelshift_r(R.v[b0 / 4], R.v[b0 / 4 + 1], (b0 % 4) * 8);
+            const uint32_t g1w = __funnelshift_r(R.v[b0 / 4 + 1], R.v[b0 / 4 + 2], (b0 % 4) * 8);
+            const uint32_t g2w = __funnelshift_r(R.v[b0 / 4 + 2], R.v[b0 / 4 + 3 <= KG ? b0 / 4 + 3 : KG], (b0 % 4) * 8);
+            const int g = gq + u;
+            const bool valid = g >= 0 && g < ng;
+            const uint32_t base = tab[valid ? g : 0] + 4;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t x = prmt(g0w, g1w, a.row_sel[2 * j]);
+                const uint32_t row = prmt(x, g2w, a.row_sel[2 * j + 1]);
+                R.rw[u][j] = row;
+                if (valid) sts32(box + base + (j + 1) * a.Px, row);
+            }
+        }
+    }
+
+    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *box,
+                                   const uint32_t *tab, Regs &R)
+    {
+        if (R.gq == INT_MIN) return;
+        const int ng = a.ntab;
+        uint32_t T[KG + 1];
+#pragma unroll
+        for (int i = 0; i <= KG; ++i) T[i] = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int g = R.gq + u;
+            const uint32_t base = tab[(g >= 0 && g < ng) ? g : 0];
+            uint32_t lo[6], hi[6];
+            // window rows 0 and 5 from the box; rows 1..4 reuse this group's
+            // own block rows held in registers
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                const uint8_t *rp = box + base + r * a.Px;
+                const uint32_t w0 = lds32(rp);
+                const uint32_t w1 = (r >= 1 && r <= 4) ? R.rw[u][r - 1] : lds32(rp + 4);
+                const uint32_t w2 = lds32(rp + 8);
+                lo[r] = __funnelshift_r(w0, w1, 24);
+                hi[r] = __funnelshift_r(w1, w2, 24);
+            }
+            // vertical 3-row sums with shared pairs, then 3-column sums
+            const uint32_t pl01 = lo[0] + lo[1], pl23 = lo[2] + lo[3], pl45 = lo[4] + lo[5];
+            const uint32_t ph01 = hi[0] + hi[1], ph23 = hi[2] + hi[3], ph45 = hi[4] + hi[5];
+            const uint32_t vl[4] = {pl01 + lo[2], lo[1] + pl23, pl23 + lo[4], lo[3] + pl45};
+            const uint32_t vh[4] = {ph01 + hi[2], hi[1] + ph23, ph23 + hi[4], hi[3] + ph45};
+            uint32_t S[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                S[j] = vl[j] + __funnelshift_r(vl[j], vh[j], 8) + __funnelshift_r(vl[j], vh[j], 16);
+            // block sums -> the group's 9 cells in omega order, merged into
+            // the unit's totals at byte 9u
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const uint32_t x = prmt(S[0], S[1], a.pack_sel[3 * m]);
+                const uint32_t y = prmt(S[2], S[3], a.pack_sel[3 * m + 1]);
+                const uint32_t tg = prmt(x, y, a.pack_sel[3 * m + 2]);
+                const int b = KG * u + 4 * m;
+                if (b / 4 <= KG) {
+                    T[b / 4] |= tg << ((b % 4) * 8);
+                    if ((b % 4) && b / 4 + 1 <= KG) T[b / 4 + 1] |= tg >> (32 - (b % 4) * 8);
+                }
+            }
+        }
+        uint8_t *op = io.ostage + io.a_out + KG * R.gq;   // word aligned; may start in the padding
+#pragma unroll
+        for (int i = 0; i < KG; ++i) sts32(op + 4 * i, rule4(a.lut, T[i], R.v[i]));
+    }
+};
+
+template <int DIM, int MODE>
+struct PolicyOf;
+template <int DIM>
+struct PolicyOf<DIM, kModeCell> { using type = CellPolicy<DIM>; };
+template <>
+struct PolicyOf<2, kModeGroup3> { using type = GroupPolicy<3>; };
+template <>
+struct PolicyOf<2, kModeGroup4> { using type = GroupPolicy<4>; };
+template <>
+struct PolicyOf<2, kModeQuad> { using type = QuadPolicy; };
+
+// Issue the bulk loads of tile T into one stage: the table row and the
+// 16-byte-aligned part of the tile's bytes that lies inside the buffer.
+__device__ __forceinline__ void issue_tile(const StepArgs &a, const uint8_t *in, int64_t T,
+                                           uint8_t *stage, uint64_t *bar)
+{
+    const uintptr_t start = (uintptr_t)(in + T * a.KL);
+    const uintptr_t end = start + (uintptr_t)a.KL;
+    const uintptr_t lo = start & ~(uintptr_t)15;
+    const uintptr_t in_lo = ((uintptr_t)in + 15) & ~(uintptr_t)15;
+    const uintptr_t in_hi = ((uintptr_t)in + (uintptr_t)a.cells) & ~(uintptr_t)15;
+    uintptr_t b0 = lo > in_lo ? lo : in_lo;
+    uintptr_t b1 = ((end + 15) & ~(uintptr_t)15);
+    if (b1 > in_hi) b1 = in_hi;
+    const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
+    const uint32_t data_bytes = b1 > b0 ? (uint32_t)(b1 - b0) : 0u;
+    mbar_arrive_expect_tx(bar, row_bytes + data_bytes);
+    bulk_g2s(stage, a.nbr + T * a.nbrw, row_bytes, bar);
+    if (data_bytes) bulk_g2s(stage + row_bytes + kStagePad + (b0 - lo), (const void *)b0, data_bytes, bar);
+}
+
+template <int DIM, int MODE>
 __global__ void __launch_bounds__(256)
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
+    using Pol = typename PolicyOf<DIM, MODE>::type;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.off_bar);
     uint8_t *box = smem + a.off_box;
     uint32_t *tab = reinterpret_cast<uint32_t *>(smem + a.off_tab);
-    uint8_t *ostage = smem + a.off_out;
-    constexpr int NDIR = (DIM == 3) ? 27 : 9;
+    uint8_t *ostage = smem + a.off_out + kStagePad;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int64_t G = gridDim.x;
     const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
@@ -478,19 +794,15 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
     for (int i = tid; i < a.ntab; i += nth) tab[i] = a.tab[i];
     __syncthreads();
 
-    int nb[NDIR - 1];
-    if (SG == 0) {
-        const int PX = a.Px, PXY = a.Px * a.Py;
-        int e = 0;
-        for (int q = 0; q < NDIR; ++q) {
-            int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = (DIM == 3) ? q / 9 - 1 : 0;
-            if (dx == 0 && dy == 0 && dz == 0) continue;
-            nb[e++] = dx + PX * dy + PXY * dz;
-        }
-    }
+    typename Pol::Regs R;
+    Pol::init(a, R);
 
     const uintptr_t in_lo = ((uintptr_t)in + 15) & ~(uintptr_t)15;
     const uintptr_t in_hi = ((uintptr_t)in + (uintptr_t)a.cells) & ~(uintptr_t)15;
+    uint32_t rv[kRingRegs];   // prefetched halo values of the current tile
+#pragma unroll
+    for (int k = 0; k < kRingRegs; ++k) rv[k] = 0;
+    bool pref = false;
 
     int64_t i = 0;
     for (int64_t T = blockIdx.x; T < a.NT; T += G, ++i) {
@@ -506,7 +818,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         const uintptr_t start = (uintptr_t)(in + T * a.KL);
         const uintptr_t end = start + (uintptr_t)a.KL;
         const uintptr_t lo = start & ~(uintptr_t)15;
-        uint8_t *data = stage + row_bytes;           // data[j] <-> address lo + j
+        uint8_t *data = stage + row_bytes + kStagePad;   // data[j] <-> address lo + j
         // bytes of the tile the bulk copy could not cover (unaligned buffer ends)
         uintptr_t b0 = lo > in_lo ? lo : in_lo;
         uintptr_t b1 = (end + 15) & ~(uintptr_t)15;
@@ -518,22 +830,58 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
             }
             __syncthreads();
         }
-        const uint8_t *tin = data + (start - lo);
-        if (SG == 0) {
-            for (int64_t l = tid; l < a.KL; l += nth) box[tab[l]] = tin[l] != 0;
-        } else {
-            for (int g = tid; g < a.ntab; g += nth) {
-                const uint32_t base = tab[g];
-                const uint8_t *src = tin + (int64_t)g * a.KG;
-                for (int lid = 0; lid < a.KG; ++lid) box[base + a.rel_of_lid[lid]] = src[lid] != 0;
+        const uintptr_t ostart = (uintptr_t)(out + T * a.KL);
+        const uintptr_t oend = ostart + (uintptr_t)a.KL;
+        const uintptr_t olo = ostart & ~(uintptr_t)15;
+        TileIO io;
+        io.data = data;
+        io.ostage = ostage;
+        io.a_in = (int)(start - lo);
+        io.a_out = (int)(ostart - olo);
+
+        Pol::scatter(a, io, box, tab, R);
+        // halo cells: the first kRingRegs per thread were prefetched during the
+        // previous tile (when `pref`), the rest are loaded now
+#pragma unroll
+        for (int k = 0; k < kRingRegs; ++k) {
+            const int e = tid + k * nth;
+            if (e < a.nring) {
+                const uint32_t w0 = __ldg(a.ring + 2 * e);
+                uint32_t v = rv[k];
+                if (!pref) {
+                    const int32_t t = nrow[w0 >> 24];
+                    v = (t >= 0) ? in[(int64_t)t * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+                }
+                box[w0 & 0xffffff] = v != 0;
             }
         }
-        for (int e = tid; e < a.nring; e += nth) {
+        for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
             const uint32_t w0 = __ldg(a.ring + 2 * e), lw = __ldg(a.ring + 2 * e + 1);
             const int32_t t = nrow[w0 >> 24];
             uint8_t v = 0;
             if (t >= 0) v = in[(int64_t)t * a.KL + lw] != 0;
             box[w0 & 0xffffff] = v;
+        }
+        // prefetch the next tile's halo values when its stage has already
+        // landed (never wait for it here); the loads stay in flight while
+        // this tile is computed
+        pref = false;
+        if (tid < a.nring && T + G < a.NT) {
+            const int sn = (int)((i + 1) % a.nstage);
+            const uint32_t pn = (uint32_t)(((i + 1) / a.nstage) & 1);
+            if (mbar_test(&bars[sn], pn)) {
+                const int32_t *nrow_n = reinterpret_cast<const int32_t *>(smem + sn * a.stage_bytes);
+#pragma unroll
+                for (int k = 0; k < kRingRegs; ++k) {
+                    const int e = tid + k * nth;
+                    if (e < a.nring) {
+                        const uint32_t w0 = __ldg(a.ring + 2 * e);
+                        const int32_t t = nrow_n[w0 >> 24];
+                        rv[k] = (t >= 0) ? in[(int64_t)t * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+                    }
+                }
+                pref = true;
+            }
         }
         if (tid == 0) bulk_wait_read_all();   // previous tile's bulk store has read ostage
         __syncthreads();
@@ -543,24 +891,9 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
             fence_proxy_async_smem();
             if (Tn < a.NT) issue_tile(a, in, Tn, stage, &bars[s]);
         }
-        const uintptr_t ostart = (uintptr_t)(out + T * a.KL);
-        const uintptr_t oend = ostart + (uintptr_t)a.KL;
-        const uintptr_t olo = ostart & ~(uintptr_t)15;
-        uint8_t *tout = ostage + (ostart - olo);
-        if (SG == 0) {
-            for (int64_t l = tid; l < a.KL; l += nth) {
-                const int p = tab[l];
-                int cnt = 0;
-#pragma unroll
-                for (int e = 0; e < NDIR - 1; ++e) cnt += box[p + nb[e]];
-                const uint32_t mask = box[p] ? a.survive : a.birth;
-                tout[l] = (mask >> cnt) & 1u;
-            }
-        } else {
-            for (int g = tid; g < a.ntab; g += nth)
-                group_compute<(SG > 0 ? SG : 3)>(a, box, tab[g], tout + (int64_t)g * a.KG);
-        }
+        Pol::compute(a, io, box, tab, R);
         __syncthreads();
+        uint8_t *tout = ostage + io.a_out;
         const uintptr_t c0 = (ostart + 15) & ~(uintptr_t)15;
         const uintptr_t c1 = oend & ~(uintptr_t)15;
         if (tid == 0) {
@@ -583,6 +916,26 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         }
     }
     if (tid == 0) bulk_wait_all();
+}
+
+// Byte tables of the rule for the quad policy (see rule4).
+static void rule_tables(uint32_t birth, uint32_t survive, uint32_t lut[4])
+{
+    uint8_t dead[8], live[8];
+    for (int j = 0; j < 8; ++j) {
+        // dead cell: total = live neighbours (<= 8)
+        uint8_t d = (birth >> j) & 1u;
+        if (j + 8 <= 8 && ((birth >> (j + 8)) & 1u)) d |= 0x80;
+        // live cell: total = live neighbours + 1 (1..9)
+        uint8_t l = (j >= 1) ? ((survive >> (j - 1)) & 1u) : 0u;
+        if (j + 8 <= 9 && ((survive >> (j + 7)) & 1u)) l |= 0x80;
+        dead[j] = d;
+        live[j] = l;
+    }
+    lut[0] = dead[0] | dead[1] << 8 | dead[2] << 16 | (uint32_t)dead[3] << 24;
+    lut[1] = dead[4] | dead[5] << 8 | dead[6] << 16 | (uint32_t)dead[7] << 24;
+    lut[2] = live[0] | live[1] << 8 | live[2] << 16 | (uint32_t)live[3] << 24;
+    lut[3] = live[4] | live[5] << 8 | live[6] << 16 | (uint32_t)live[7] << 24;
 }
 
 int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
@@ -612,21 +965,98 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
     a.nbr = p.nbr;
     a.birth = birth;
     a.survive = survive;
+    rule_tables(birth, survive, a.lut);
     a.status = f->status;
     for (int q = 0; q < kMaxGroup; ++q) {
         a.lid_of_q[q] = p.lid_of_q[q];
         a.rel_of_lid[q] = p.rel_of_lid[q];
     }
+    for (int q = 0; q < 8; ++q) a.row_sel[q] = p.row_sel[q];
+    for (int q = 0; q < 9; ++q) a.pack_sel[q] = p.pack_sel[q];
     if (f->dim == 3)
-        step_tma_kernel<3, 0><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
-    else if (p.mode == 4)
-        step_tma_kernel<2, 4><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
-    else if (p.mode == 3)
-        step_tma_kernel<2, 3><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+        step_tma_kernel<3, kModeCell><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (p.mode == kModeQuad)
+        step_tma_kernel<2, kModeQuad><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (p.mode == kModeGroup4)
+        step_tma_kernel<2, kModeGroup4><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (p.mode == kModeGroup3)
+        step_tma_kernel<2, kModeGroup3><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else
-        step_tma_kernel<2, 0><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+        step_tma_kernel<2, kModeCell><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     FR_CUDA(cudaGetLastError());
     return FR_OK;
+}
+
+// ---------------------------------------------------------------- autotune
+
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;  // fractal + device -> tile levels
+
+static std::string tune_key(const fractal *f)
+{
+    cudaDeviceProp prop;
+    std::string name = "?";
+    if (cudaGetDeviceProperties(&prop, f->device) == cudaSuccess) name = prop.name;
+    std::string key = name + "|" + std::to_string(f->k) + "," + std::to_string(f->s) + "," +
+                      std::to_string(f->r) + "," + std::to_string(f->dim) + "|";
+    for (int32_t v : f->offsets) key += std::to_string(v) + ",";
+    return key;
+}
+
+int cached_tile_levels(const fractal *f)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(f));
+    return it == g_tune_cache.end() ? -1 : it->second;
+}
+
+// Times the candidate tile depths (the deepest that fit in shared memory and
+// the three below) on the caller's buffers and keeps the fastest.
+int autotune_step(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth, uint32_t survive,
+                  cudaStream_t st, int *best_out)
+{
+    int lmax = 0;
+    for (int L = 0; L <= f->r; ++L) {
+        if (plan_layout(f, L).total > 200 * 1024) break;
+        lmax = L;
+    }
+    int best = -1;
+    float best_ms = 0.f;
+    cudaEvent_t e0, e1;
+    FR_CUDA(cudaEventCreate(&e0));
+    FR_CUDA(cudaEventCreate(&e1));
+    for (int L = lmax; L >= 0 && L >= lmax - 3; --L) {
+        if (ipow(f->k, f->r - L) >= ((int64_t)1 << 31)) break;
+        f->tile_levels_user = L;
+        if (ensure_step_plan(f) != FR_OK) continue;
+        int rc = FR_OK;
+        for (int w = 0; w < 2 && !rc; ++w) rc = launch_step_once(f, in, out, birth, survive, st);
+        if (!rc) rc = (cudaEventRecord(e0, st) == cudaSuccess) ? FR_OK : FR_ECUDA;
+        for (int w = 0; w < 3 && !rc; ++w) rc = launch_step_once(f, in, out, birth, survive, st);
+        if (!rc) rc = (cudaEventRecord(e1, st) == cudaSuccess) ? FR_OK : FR_ECUDA;
+        if (!rc) rc = (cudaEventSynchronize(e1) == cudaSuccess) ? FR_OK : FR_ECUDA;
+        float ms = 0.f;
+        if (!rc && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best < 0 || ms < best_ms)) {
+            best = L;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) {
+        f->tile_levels_user = -1;
+        set_error(FR_EINVAL, "fractal_autotune: no tile depth could be planned");
+        return FR_EINVAL;
+    }
+    f->tile_levels_user = best;
+    int rc = ensure_step_plan(f);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[tune_key(f)] = best;
+    }
+    if (best_out) *best_out = best;
+    return take_status(f);
 }
 
 }  // namespace fr

@@ -156,6 +156,18 @@ class Fractal:
     def tile_levels(self, levels: int):
         self._check(self._lib.fractal_set_tile_levels(self._h, int(levels)))
 
+    def autotune(self, state: torch.Tensor, out: torch.Tensor | None = None, rule=None,
+                 stream=None) -> int:
+        """Pick the fastest tile depth on these buffers (``fractal_autotune``);
+        ``out`` is overwritten.  Returns the chosen depth."""
+        birth, survive = rule if rule is not None else self.default_rule()
+        out = out if out is not None else torch.empty_like(state)
+        v = ctypes.c_int()
+        self._check(self._lib.fractal_autotune(self._h, _dev_ptr(state, torch.uint8, "state_in"),
+                                               _dev_ptr(out, torch.uint8, "state_out"), birth, survive,
+                                               _stream(stream), ctypes.byref(v)))
+        return v.value
+
     def default_rule(self):
         return (0x20, 0x30) if self.dim == 3 else LIFE_B3S23
 

@@ -145,6 +145,20 @@ def test_step_exhaustive_all_tile_depths(P, fam, r, levels):
         assert np.array_equal(out.cpu().numpy(), ref), f"L={L}"
 
 
+def test_autotune_keeps_parity(P):
+    fam, r = W.TRIANGLE, 11
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(31, 0.4)
+    x = torch.from_numpy(init).cuda()
+    scratch = torch.empty_like(x)
+    L = g.autotune(x, scratch)
+    assert 0 <= L <= r and g.tile_levels == L
+    assert np.array_equal(x.cpu().numpy(), init)
+    assert np.array_equal(g.step(x, steps=3).cpu().numpy(), o.step(init, steps=3))
+    # a new handle of the same fractal starts from the tuned depth
+    assert gpu_fr(P, fam, r).tile_levels == L
+
+
 @pytest.mark.parametrize("steps", [0, 1, 2, 3, 4])
 def test_step_ping_pong_counts(P, steps):
     fam, r = W.VICSEK, 5
