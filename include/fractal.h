@@ -122,6 +122,30 @@ int fractal_step(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
                  int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
                  void *stream);
 
+/* fractal_step without any device allocation (the paper has no counterpart:
+ * this serves callers that must not allocate device memory while they run,
+ * such as code being captured into a CUDA graph under a capture mode that
+ * forbids cudaMalloc, or applications whose device memory is fixed up
+ * front).  Same arguments and results as fractal_step, but:
+ *   - the ping-pong buffer for steps > 1 is a fixed 32 MiB device array
+ *     inside the library (held on every GPU that loads the library until the
+ *     process exits), so k^r must be at most 33,554,432 cells; larger states
+ *     are rejected with FR_EINVAL;
+ *   - the handle's tables must already exist: they are built (and
+ *     allocated) by the handle's first fractal_step, fractal_autotune or
+ *     fractal_get_tile_levels call; otherwise FR_EINVAL;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture;
+ *   - the array is shared by every call in the process and keeps the last
+ *     call's contents (no call needs it to start at zero: each generation
+ *     overwrites it completely before it is read); calls whose work overlaps
+ *     on the GPU (other streams, other host threads) race on it and must be
+ *     serialised by the caller. */
+int fractal_step_noalloc(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
+                         int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
+                         void *stream);
+
 /* The bounding-box approach (Sec. 4, "BB"): the same rule applied to every
  * cell of the n^dim box.  Cells off the fractal count as dead whatever their
  * byte and are written as 0.  box_in_dev / box_out_dev: n^dim bytes each,
