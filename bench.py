@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bb", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile-levels", type=int, default=-1, help="tile depth L (-1: library choice)")
     return ap.parse_args()
@@ -321,6 +324,9 @@ def run_ours(args, rank, world, dist):
     # compact vs bounding box at equal r
     if not args.no_bb and rank == 0:
         extra["bb_compare"] = bb_compare(args, W)
+    # many uneven instances: batched graph vs one instance per launch
+    if not args.no_batch and rank == 0:
+        extra["batched"] = batched_compare(args, W)
 
     gpu_launches = args.steps  # one step-kernel launch per generation
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -369,6 +375,73 @@ def bb_compare(args, W):
            "generations_timed": n}
     del st, out, box, box_out, flush_buf
     g.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def batched_compare(args, W):
+    """4096 uneven independent instances (triangle r 6..14, carpet r 3..8,
+    Vicsek r 3..9, p ~ U[0.2, 0.6], seeds from master seed 7), 200 generations
+    each: the batched graph-replayed run against the loop of one
+    fractal_step call per instance."""
+    import torch
+    from paper_2110_12952_gb300 import Batch, Fractal
+    mix = W.batched_mix(args.batch_instances, master_seed=7, steps=args.batch_steps)
+    handles = {}
+    states = []
+    for inst in mix:
+        key = (inst.family.name, inst.r)
+        if key not in handles:
+            handles[key] = Fractal.from_family(inst.family, inst.r)
+        g = handles[key]
+        x = g.init_bernoulli(inst.seed, inst.p)
+        states.append((g, x, torch.empty_like(x)))
+    for g in handles.values():   # tile depth per fractal and level (untimed)
+        x = g.init_bernoulli(1, 0.5)
+        g.autotune(x, torch.empty_like(x))
+        del x
+    batch = Batch()
+    for (g, x, y), inst in zip(states, mix):
+        batch.add(g, x, y, inst.steps)
+    batch.run()                    # builds tables and graph; untimed
+    torch.cuda.synchronize()
+    updates, launches = batch.stats()
+    st = torch.cuda.current_stream()
+    best_b = None
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        batch.run()
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best_b = ms if best_b is None else min(best_b, ms)
+    ref = [y.clone() for (_, _, y) in states[:64]]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(st)
+    for (g, x, y), inst in zip(states, mix):
+        g.step(x, out=y, steps=inst.steps)
+    e1.record(st)
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    plain_wall = time.perf_counter() - t0
+    same = all(torch.equal(a, y) for a, (_, _, y) in zip(ref, states[:64]))
+    total_cells = sum(i.cells for i in mix)
+    res = {"workload": f"{len(mix)} instances (triangle r6-14, carpet r3-8, vicsek r3-9), "
+                       f"{args.batch_steps} generations each, master seed 7",
+           "total_cells": total_cells, "cell_updates": updates,
+           "batched_ms": best_b, "batched_updates_per_s": updates / (best_b / 1e3),
+           "batched_launches_in_graph": launches, "graph_launches_per_run": 1,
+           "plain_ms": plain_ms, "plain_wall_s": plain_wall,
+           "plain_updates_per_s": updates / (plain_ms / 1e3),
+           "plain_launches": sum(i.steps for i in mix),
+           "speedup_batched_vs_plain": plain_ms / best_b,
+           "batched_equals_plain_on_sample": bool(same)}
+    batch.close()
+    del states, ref
+    for g in handles.values():
+        g.close()
     torch.cuda.empty_cache()
     return res
 

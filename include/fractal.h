@@ -187,6 +187,35 @@ int fractal_autotune(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
                      uint32_t birth_mask, uint32_t survive_mask, void *stream,
                      int *levels);
 
+/* ---- Batched execution of many independent instances ------------------
+ * (not in the paper: it fuses the generations of many uneven instances so
+ * that small instances do not pay one launch each per generation).
+ *
+ * A batch holds instances (handle, in, out, steps, rule).  fractal_batch_run
+ * advances every instance by its own number of generations, exactly as
+ * fractal_step(handle, in, out, steps, rule) would, but with one kernel
+ * launch per generation for all instances that share a fractal and tile
+ * depth, and the whole run captured into one CUDA graph that is launched on
+ * `stream` (asynchronously).  The graph is kept and replayed by later runs
+ * until instances are added or cleared.  Buffers stay owned by the caller and
+ * must stay valid while a run is in flight; the batch owns a device arena for
+ * its tables and for one k^r-byte ping-pong buffer per instance with
+ * steps > 1.  Handles must outlive the batch's runs.  Before the first run
+ * (and after any change) the batch builds its tables and the graph: that run
+ * allocates and waits for the device, so make it before any stream capture. */
+typedef struct fractal_batch fractal_batch_t;
+int fractal_batch_create(fractal_batch_t **out);
+int fractal_batch_destroy(fractal_batch_t *b);
+/* Adds an instance; in_dev / out_dev: k^r bytes each, not overlapping.
+ * *id (if not NULL) receives its index in the batch. */
+int fractal_batch_add(fractal_batch_t *b, fractal_t *f, const uint8_t *in_dev,
+                      uint8_t *out_dev, int64_t steps, uint32_t birth_mask,
+                      uint32_t survive_mask, int64_t *id);
+int fractal_batch_clear(fractal_batch_t *b);
+int fractal_batch_run(fractal_batch_t *b, void *stream);
+/* Cell updates and kernel launches of the last built run. */
+int fractal_batch_stats(const fractal_batch_t *b, int64_t *updates, int64_t *launches);
+
 /* Waits for `stream` and reports any asynchronous CUDA error. */
 int fractal_sync(void *stream);
 

@@ -11,13 +11,16 @@ Importing the package does not load the CUDA library; the first ``Fractal``
 does, and raises if ``libfractal.so`` has not been built.
 """
 
-__all__ = ["Fractal", "FractalError", "build", "workloads"]
+__all__ = ["Fractal", "Batch", "FractalError", "build", "workloads"]
 
 
 def __getattr__(name):
     if name == "Fractal":
         from .fractal import Fractal
         return Fractal
+    if name == "Batch":
+        from .fractal import Batch
+        return Batch
     if name == "FractalError":
         from .capi import FractalError
         return FractalError

@@ -51,6 +51,12 @@ SIGNATURES = {
     "fractal_sync": (c_int, [c_vp]),
     "fractal_check": (c_int, [c_fp]),
     "fractal_step_noalloc": (c_int, [c_fp, c_vp, c_vp, c_i64, c_u32, c_u32, c_vp]),
+    "fractal_batch_create": (c_int, [ctypes.POINTER(c_vp)]),
+    "fractal_batch_destroy": (c_int, [c_vp]),
+    "fractal_batch_add": (c_int, [c_vp, c_fp, c_vp, c_vp, c_i64, c_u32, c_u32, c_i64p]),
+    "fractal_batch_clear": (c_int, [c_vp]),
+    "fractal_batch_run": (c_int, [c_vp, c_vp]),
+    "fractal_batch_stats": (c_int, [c_vp, c_i64p, c_i64p]),
     "fractal_autotune": (c_int, [c_fp, c_vp, c_vp, c_u32, c_u32, c_vp, ctypes.POINTER(c_int)]),
 }
 

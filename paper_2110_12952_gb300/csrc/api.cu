@@ -43,7 +43,8 @@ static bool mul_ok(int64_t a, int64_t b, int64_t limit, int64_t *out)
     return true;
 }
 
-int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st);
+int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, int num_sms, cudaStream_t st);
+int preload_copy_kernel();
 
 int ensure_status(fractal *f)
 {
@@ -231,7 +232,7 @@ extern "C" int fractal_step(fractal_t *f, const uint8_t *in, uint8_t *out, int64
     if (steps < 0) return fail(FR_EINVAL, "fractal_step: steps < 0");
     if (overlap(in, out, f->cells)) return fail(FR_EINVAL, "fractal_step: in and out overlap");
     cudaStream_t st = (cudaStream_t)stream;
-    if (steps == 0) return launch_copy_normalise(in, out, f->cells, st);
+    if (steps == 0) return launch_copy_normalise(in, out, f->cells, f->num_sms, st);
     int rc = ensure_step_plan(f);
     if (rc) return rc;
     if (steps > 1) {

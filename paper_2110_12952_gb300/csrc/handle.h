@@ -36,6 +36,7 @@ struct StepPlan {
     int smem = 0;          // dynamic shared memory per CTA
     int block = 256;
     int grid = 0;
+    int per_sm = 0;        // resident CTAs per SM
     int mode = 0;          // 0: per-cell neighbour reads; 3 or 4: group mode, block side s^G
     int G = 0;             // levels per group (group mode)
     int KG = 0;            // k^G cells per group
@@ -90,7 +91,8 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
                      uint32_t survive, cudaStream_t st);
 int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                    uint32_t survive, cudaStream_t st);
-int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st);
+int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, int num_sms, cudaStream_t st);
+int preload_copy_kernel();
 int ensure_status(fractal *f);
 int take_status(fractal *f);
 int cached_tile_levels(const fractal *f);

@@ -157,19 +157,20 @@ __global__ void copy_normalise_kernel(const uint8_t *__restrict__ in, uint8_t *_
         out[i] = in[i] != 0;
 }
 
-static int num_sms_current()
-{
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
-
-int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t st)
+int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, int num_sms, cudaStream_t st)
 {
     if (n == 0) return FR_OK;
-    copy_normalise_kernel<<<grid_for(n, 256, num_sms_current()), 256, 0, st>>>(in, out, n);
+    copy_normalise_kernel<<<grid_for(n, 256, num_sms), 256, 0, st>>>(in, out, n);
     FR_CUDA(cudaGetLastError());
+    return FR_OK;
+}
+
+// Loads the copy kernel's module now, so that a first launch inside a stream
+// capture does not have to.
+int preload_copy_kernel()
+{
+    cudaFuncAttributes fa;
+    FR_CUDA(cudaFuncGetAttributes(&fa, copy_normalise_kernel));
     return FR_OK;
 }
 

@@ -82,7 +82,7 @@ extern "C" int fractal_step_noalloc(fractal_t *f, const uint8_t *in, uint8_t *ou
         return FR_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (steps == 0) return launch_copy_normalise(in, out, f->cells, st);
+    if (steps == 0) return launch_copy_normalise(in, out, f->cells, f->num_sms, st);
     int dev = 0;
     FR_CUDA(cudaGetDevice(&dev));
     if (dev != f->device) {

@@ -49,6 +49,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "step.h"
 #include "tma.cuh"
 
 namespace fr {
@@ -67,9 +68,12 @@ struct StepArgs {
     const uint32_t *tab;   // cell mode: box offset per cell; else window base per group
     const uint32_t *ring;
     const int32_t *nbr;
-    uint32_t birth, survive;
-    uint32_t lut[4];       // quad mode: rule as byte tables (dead lo/hi, live lo/hi)
+    Rule rule;             // single-instance launches
     int *status;
+    // multi-instance launches (tile_inst != nullptr)
+    const int32_t *tile_inst;
+    const InstDesc *insts;
+    int gen;
     int8_t lid_of_q[kMaxGroup];     // block position -> cell of the group, -1 none
     int16_t rel_of_lid[kMaxGroup];  // cell of the group -> box offset from the window base
     uint32_t row_sel[8];            // quad: cells -> block row j (two selectors per row)
@@ -262,20 +266,31 @@ __global__ void nbr_table_kernel(FracDev F, int64_t NT, int coarse_levels, int32
     }
 }
 
-template <int DIM, int MODE>
+template <int DIM, int MODE, bool MULTI>
 __global__ void step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in,
                                 uint8_t *__restrict__ out);
 
+// The dynamic shared-memory limit is a property of the kernel function, shared
+// by every handle: it is raised to the device's opt-in maximum (never set to
+// one plan's size, which would break plans that need more).
 template <int DIM, int MODE>
 static int configure(StepPlan &p, int num_sms)
 {
-    int per_sm = 0;
-    FR_CUDA(cudaFuncSetAttribute(step_tma_kernel<DIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
-    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tma_kernel<DIM, MODE>, p.block, p.smem));
+    int per_sm = 0, dev = 0, optin = 0;
+    FR_CUDA(cudaGetDevice(&dev));
+    FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (p.smem > optin) {
+        set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
+        return FR_EINVAL;
+    }
+    FR_CUDA(cudaFuncSetAttribute(step_tma_kernel<DIM, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_tma_kernel<DIM, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tma_kernel<DIM, MODE, false>, p.block, p.smem));
     if (per_sm < 1) {
         set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
         return FR_EINVAL;
     }
+    p.per_sm = per_sm;
     p.grid = (int)std::min<int64_t>((int64_t)per_sm * num_sms, p.NT);
     return FR_OK;
 }
@@ -529,8 +544,9 @@ __device__ __forceinline__ void load_window(const uint8_t *box, uint32_t ad0, in
 
 // New states of the cells of one group from its window (byte stores).
 template <int SG>
-__device__ __forceinline__ void group_from_window(const StepArgs &a, const uint32_t *lo,
-                                                  const uint32_t *hi, uint8_t *gout)
+__device__ __forceinline__ void group_from_window(const StepArgs &a, const Rule &rule,
+                                                  const uint32_t *lo, const uint32_t *hi,
+                                                  uint8_t *gout)
 {
 #pragma unroll
     for (int j = 0; j < SG; ++j) {
@@ -545,7 +561,7 @@ __device__ __forceinline__ void group_from_window(const StepArgs &a, const uint3
             if (lid >= 0) {
                 const uint32_t al = (alive >> (8 * c)) & 1u;
                 const uint32_t cnt = ((sum >> (8 * c)) & 0xffu) - al;
-                gout[lid] = ((al ? a.survive : a.birth) >> cnt) & 1u;
+                gout[lid] = ((al ? rule.survive : rule.birth) >> cnt) & 1u;
             }
         }
     }
@@ -555,6 +571,7 @@ struct TileIO {
     const uint8_t *data;   // 16-byte aligned stage data; tile cell l at data[a_in + l]
     uint8_t *ostage;       // 16-byte aligned output stage; tile cell l at ostage[a_out + l]
     int a_in, a_out;
+    Rule rule;             // the rule of the tile's instance
 };
 
 // ---- cell policy
@@ -587,7 +604,7 @@ struct CellPolicy {
             int cnt = 0;
 #pragma unroll
             for (int e = 0; e < NDIR - 1; ++e) cnt += box[p + R.nb[e]];
-            const uint32_t mask = box[p] ? a.survive : a.birth;
+            const uint32_t mask = box[p] ? io.rule.survive : io.rule.birth;
             tout[l] = (mask >> cnt) & 1u;
         }
     }
@@ -615,7 +632,7 @@ struct GroupPolicy {
         for (int g = threadIdx.x; g < a.ntab; g += blockDim.x) {
             uint32_t lo[SG + 2], hi[SG + 2];
             load_window<SG>(box, tab[g], a.Px, lo, hi);
-            group_from_window<SG>(a, lo, hi, tout + (int64_t)g * a.KG);
+            group_from_window<SG>(a, io.rule, lo, hi, tout + (int64_t)g * a.KG);
         }
     }
 };
@@ -732,7 +749,7 @@ struct QuadPolicy {
         }
         uint8_t *op = io.ostage + io.a_out + KG * R.gq;   // word aligned; may start in the padding
 #pragma unroll
-        for (int i = 0; i < KG; ++i) sts32(op + 4 * i, rule4(a.lut, T[i], R.v[i]));
+        for (int i = 0; i < KG; ++i) sts32(op + 4 * i, rule4(io.rule.lut, T[i], R.v[i]));
     }
 };
 
@@ -747,27 +764,70 @@ struct PolicyOf<2, kModeGroup4> { using type = GroupPolicy<4>; };
 template <>
 struct PolicyOf<2, kModeQuad> { using type = QuadPolicy; };
 
-// Issue the bulk loads of tile T into one stage: the table row and the
-// 16-byte-aligned part of the tile's bytes that lies inside the buffer.
-__device__ __forceinline__ void issue_tile(const StepArgs &a, const uint8_t *in, int64_t T,
-                                           uint8_t *stage, uint64_t *bar)
+// A tile of the launch resolved to its instance's buffers, table and rule.
+struct TileRef {
+    const uint8_t *in;
+    uint8_t *out;
+    const int32_t *nbr;
+    int64_t cells;
+    int64_t T;            // tile index within the instance
+};
+
+template <bool MULTI>
+__device__ __forceinline__ TileRef resolve(const StepArgs &a, const uint8_t *in, uint8_t *out,
+                                           int64_t Tg)
 {
-    const uintptr_t start = (uintptr_t)(in + T * a.KL);
+    TileRef t;
+    if (!MULTI) {
+        t.in = in;
+        t.out = out;
+        t.nbr = a.nbr;
+        t.cells = a.cells;
+        t.T = Tg;
+    } else {
+        const InstDesc *d = a.insts + __ldg(a.tile_inst + Tg);
+        if (a.gen & 1) {
+            t.in = (a.gen == 1) ? d->first : d->even_dst;
+            t.out = d->odd_dst;
+        } else {
+            t.in = d->odd_dst;
+            t.out = d->even_dst;
+        }
+        t.nbr = d->nbr;
+        t.cells = d->cells;
+        t.T = Tg - d->tile0;
+    }
+    return t;
+}
+
+template <bool MULTI>
+__device__ __forceinline__ void tile_rule(const StepArgs &a, int64_t Tg, Rule &r)
+{
+    if (!MULTI) r = a.rule;
+    else r = a.insts[__ldg(a.tile_inst + Tg)].rule;
+}
+
+// Issue the bulk loads of a tile into one stage: its table row and the
+// 16-byte-aligned part of its bytes that lies inside the instance's buffer.
+__device__ __forceinline__ void issue_tile(const StepArgs &a, const TileRef &t, uint8_t *stage,
+                                           uint64_t *bar)
+{
+    const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
     const uintptr_t end = start + (uintptr_t)a.KL;
     const uintptr_t lo = start & ~(uintptr_t)15;
-    const uintptr_t in_lo = ((uintptr_t)in + 15) & ~(uintptr_t)15;
-    const uintptr_t in_hi = ((uintptr_t)in + (uintptr_t)a.cells) & ~(uintptr_t)15;
+    const uintptr_t in_lo = ((uintptr_t)t.in + 15) & ~(uintptr_t)15;
+    const uintptr_t in_hi = ((uintptr_t)t.in + (uintptr_t)t.cells) & ~(uintptr_t)15;
     uintptr_t b0 = lo > in_lo ? lo : in_lo;
     uintptr_t b1 = ((end + 15) & ~(uintptr_t)15);
     if (b1 > in_hi) b1 = in_hi;
     const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
     const uint32_t data_bytes = b1 > b0 ? (uint32_t)(b1 - b0) : 0u;
     mbar_arrive_expect_tx(bar, row_bytes + data_bytes);
-    bulk_g2s(stage, a.nbr + T * a.nbrw, row_bytes, bar);
+    bulk_g2s(stage, t.nbr + t.T * a.nbrw, row_bytes, bar);
     if (data_bytes) bulk_g2s(stage + row_bytes + kStagePad + (b0 - lo), (const void *)b0, data_bytes, bar);
 }
 
-template <int DIM, int MODE>
+template <int DIM, int MODE, bool MULTI>
 __global__ void __launch_bounds__(256)
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
@@ -785,8 +845,8 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
         fence_proxy_async_smem();
         for (int s = 0; s < a.nstage; ++s) {
-            int64_t T = blockIdx.x + s * G;
-            if (T < a.NT) issue_tile(a, in, T, smem + s * a.stage_bytes, &bars[s]);
+            const int64_t Tg = blockIdx.x + s * G;
+            if (Tg < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tg), smem + s * a.stage_bytes, &bars[s]);
         }
     }
     for (int i = tid; i < a.box_bytes / 16; i += nth)
@@ -797,15 +857,13 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
     typename Pol::Regs R;
     Pol::init(a, R);
 
-    const uintptr_t in_lo = ((uintptr_t)in + 15) & ~(uintptr_t)15;
-    const uintptr_t in_hi = ((uintptr_t)in + (uintptr_t)a.cells) & ~(uintptr_t)15;
     uint32_t rv[kRingRegs];   // prefetched halo values of the current tile
 #pragma unroll
     for (int k = 0; k < kRingRegs; ++k) rv[k] = 0;
     bool pref = false;
 
     int64_t i = 0;
-    for (int64_t T = blockIdx.x; T < a.NT; T += G, ++i) {
+    for (int64_t Tg = blockIdx.x; Tg < a.NT; Tg += G, ++i) {
         const int s = (int)(i % a.nstage);
         const uint32_t parity = (uint32_t)((i / a.nstage) & 1);
         uint8_t *stage = smem + s * a.stage_bytes;
@@ -815,7 +873,10 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
             if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
             break;
         }
-        const uintptr_t start = (uintptr_t)(in + T * a.KL);
+        const TileRef t = resolve<MULTI>(a, in, out, Tg);
+        const uintptr_t in_lo = ((uintptr_t)t.in + 15) & ~(uintptr_t)15;
+        const uintptr_t in_hi = ((uintptr_t)t.in + (uintptr_t)t.cells) & ~(uintptr_t)15;
+        const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
         const uintptr_t end = start + (uintptr_t)a.KL;
         const uintptr_t lo = start & ~(uintptr_t)15;
         uint8_t *data = stage + row_bytes + kStagePad;   // data[j] <-> address lo + j
@@ -830,7 +891,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
             }
             __syncthreads();
         }
-        const uintptr_t ostart = (uintptr_t)(out + T * a.KL);
+        const uintptr_t ostart = (uintptr_t)(t.out + t.T * a.KL);
         const uintptr_t oend = ostart + (uintptr_t)a.KL;
         const uintptr_t olo = ostart & ~(uintptr_t)15;
         TileIO io;
@@ -838,6 +899,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         io.ostage = ostage;
         io.a_in = (int)(start - lo);
         io.a_out = (int)(ostart - olo);
+        tile_rule<MULTI>(a, Tg, io.rule);
 
         Pol::scatter(a, io, box, tab, R);
         // halo cells: the first kRingRegs per thread were prefetched during the
@@ -849,35 +911,36 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
                 const uint32_t w0 = __ldg(a.ring + 2 * e);
                 uint32_t v = rv[k];
                 if (!pref) {
-                    const int32_t t = nrow[w0 >> 24];
-                    v = (t >= 0) ? in[(int64_t)t * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+                    const int32_t tn = nrow[w0 >> 24];
+                    v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
                 }
                 box[w0 & 0xffffff] = v != 0;
             }
         }
         for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
             const uint32_t w0 = __ldg(a.ring + 2 * e), lw = __ldg(a.ring + 2 * e + 1);
-            const int32_t t = nrow[w0 >> 24];
+            const int32_t tn = nrow[w0 >> 24];
             uint8_t v = 0;
-            if (t >= 0) v = in[(int64_t)t * a.KL + lw] != 0;
+            if (tn >= 0) v = t.in[(int64_t)tn * a.KL + lw] != 0;
             box[w0 & 0xffffff] = v;
         }
         // prefetch the next tile's halo values when its stage has already
         // landed (never wait for it here); the loads stay in flight while
         // this tile is computed
         pref = false;
-        if (tid < a.nring && T + G < a.NT) {
+        if (tid < a.nring && Tg + G < a.NT) {
             const int sn = (int)((i + 1) % a.nstage);
             const uint32_t pn = (uint32_t)(((i + 1) / a.nstage) & 1);
             if (mbar_test(&bars[sn], pn)) {
+                const TileRef tn_ref = resolve<MULTI>(a, in, out, Tg + G);
                 const int32_t *nrow_n = reinterpret_cast<const int32_t *>(smem + sn * a.stage_bytes);
 #pragma unroll
                 for (int k = 0; k < kRingRegs; ++k) {
                     const int e = tid + k * nth;
                     if (e < a.nring) {
                         const uint32_t w0 = __ldg(a.ring + 2 * e);
-                        const int32_t t = nrow_n[w0 >> 24];
-                        rv[k] = (t >= 0) ? in[(int64_t)t * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+                        const int32_t tn = nrow_n[w0 >> 24];
+                        rv[k] = (tn >= 0) ? tn_ref.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
                     }
                 }
                 pref = true;
@@ -887,9 +950,9 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         __syncthreads();
         // stage s is consumed: refill it with the tile nstage iterations ahead
         if (tid == 0) {
-            const int64_t Tn = T + a.nstage * G;
+            const int64_t Tn = Tg + a.nstage * G;
             fence_proxy_async_smem();
-            if (Tn < a.NT) issue_tile(a, in, Tn, stage, &bars[s]);
+            if (Tn < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tn), stage, &bars[s]);
         }
         Pol::compute(a, io, box, tab, R);
         __syncthreads();
@@ -938,11 +1001,16 @@ static void rule_tables(uint32_t birth, uint32_t survive, uint32_t lut[4])
     lut[3] = live[4] | live[5] << 8 | live[6] << 16 | (uint32_t)live[7] << 24;
 }
 
-int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
-                     uint32_t survive, cudaStream_t st)
+void make_rule(uint32_t birth, uint32_t survive, Rule *r)
+{
+    r->birth = birth;
+    r->survive = survive;
+    rule_tables(birth, survive, r->lut);
+}
+
+static void fill_args(const fractal *f, StepArgs &a)
 {
     const StepPlan &p = f->plan;
-    StepArgs a;
     a.KL = p.KL;
     a.NT = p.NT;
     a.cells = f->cells;
@@ -963,28 +1031,61 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
     a.tab = p.pos;
     a.ring = p.ring;
     a.nbr = p.nbr;
-    a.birth = birth;
-    a.survive = survive;
-    rule_tables(birth, survive, a.lut);
     a.status = f->status;
+    a.tile_inst = nullptr;
+    a.insts = nullptr;
+    a.gen = 0;
     for (int q = 0; q < kMaxGroup; ++q) {
         a.lid_of_q[q] = p.lid_of_q[q];
         a.rel_of_lid[q] = p.rel_of_lid[q];
     }
     for (int q = 0; q < 8; ++q) a.row_sel[q] = p.row_sel[q];
     for (int q = 0; q < 9; ++q) a.pack_sel[q] = p.pack_sel[q];
+}
+
+template <bool MULTI>
+static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t *in, uint8_t *out,
+                    cudaStream_t st)
+{
+    const StepPlan &p = f->plan;
     if (f->dim == 3)
-        step_tma_kernel<3, kModeCell><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+        step_tma_kernel<3, kModeCell, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeQuad)
-        step_tma_kernel<2, kModeQuad><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+        step_tma_kernel<2, kModeQuad, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup4)
-        step_tma_kernel<2, kModeGroup4><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+        step_tma_kernel<2, kModeGroup4, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup3)
-        step_tma_kernel<2, kModeGroup3><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+        step_tma_kernel<2, kModeGroup3, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else
-        step_tma_kernel<2, kModeCell><<<p.grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+        step_tma_kernel<2, kModeCell, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     FR_CUDA(cudaGetLastError());
     return FR_OK;
+}
+
+int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
+                     uint32_t survive, cudaStream_t st)
+{
+    StepArgs a;
+    fill_args(f, a);
+    make_rule(birth, survive, &a.rule);
+    return dispatch<false>(f, a, f->plan.grid, in, out, st);
+}
+
+int launch_step_multi(const fractal *cls, const InstDesc *descs, const int32_t *tile_inst,
+                      int ninst, int64_t total, int gen, cudaStream_t st)
+{
+    if (ninst <= 0 || total <= 0) return FR_OK;
+    StepArgs a;
+    fill_args(cls, a);
+    make_rule(0, 0, &a.rule);
+    a.NT = total;
+    a.cells = 0;
+    a.nbr = nullptr;
+    a.tile_inst = tile_inst;
+    a.insts = descs;
+    a.gen = gen;
+    const int grid = (int)std::min<int64_t>((int64_t)cls->plan.per_sm * cls->num_sms, total);
+    return dispatch<true>(cls, a, grid, nullptr, nullptr, st);
 }
 
 // ---------------------------------------------------------------- autotune

@@ -177,3 +177,51 @@ class Fractal:
     def check(self):
         """Raise if a bounded device-side wait of this handle gave up."""
         self._check(self._lib.fractal_check(self._h))
+
+
+class Batch:
+    """Many independent instances advanced together (``fractal_batch_*``).
+
+    ``add(fractal, state_in, state_out, steps, rule)`` queues an instance;
+    ``run()`` advances all of them, each exactly as ``Fractal.step`` would,
+    with one launch per generation for each group of instances that share a
+    fractal and tile depth, replayed from a captured CUDA graph."""
+
+    def __init__(self):
+        self._lib = capi.load()
+        h = ctypes.c_void_p()
+        capi.check(self._lib.fractal_batch_create(ctypes.byref(h)), self._lib)
+        self._h = h
+        self._keep = []   # tensors and handles that must outlive the runs
+
+    def add(self, fr: Fractal, state: torch.Tensor, out: torch.Tensor, steps: int, rule=None) -> int:
+        birth, survive = rule if rule is not None else fr.default_rule()
+        idx = ctypes.c_int64()
+        capi.check(self._lib.fractal_batch_add(self._h, fr._h, _dev_ptr(state, torch.uint8, "state"),
+                                               _dev_ptr(out, torch.uint8, "out"), steps, birth, survive,
+                                               ctypes.byref(idx)), self._lib)
+        self._keep.append((fr, state, out))
+        return idx.value
+
+    def run(self, stream=None):
+        capi.check(self._lib.fractal_batch_run(self._h, _stream(stream)), self._lib)
+
+    def clear(self):
+        capi.check(self._lib.fractal_batch_clear(self._h), self._lib)
+        self._keep = []
+
+    def stats(self):
+        u, l = ctypes.c_int64(), ctypes.c_int64()
+        capi.check(self._lib.fractal_batch_stats(self._h, ctypes.byref(u), ctypes.byref(l)), self._lib)
+        return u.value, l.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fractal_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

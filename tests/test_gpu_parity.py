@@ -159,6 +159,19 @@ def test_autotune_keeps_parity(P):
     assert gpu_fr(P, fam, r).tile_levels == L
 
 
+def test_handles_with_different_tiles_interleaved(P):
+    # the kernel's shared-memory limit is per function: a handle planned later
+    # with a smaller tile must not break an earlier handle's larger plan
+    big, small = gpu_fr(P, W.CARPET, 6), gpu_fr(P, W.CARPET, 2)
+    ob, osm = ora(W.CARPET, 6), ora(W.CARPET, 2)
+    ib, ism = ob.init_bernoulli(3, 0.5), osm.init_bernoulli(4, 0.5)
+    xb, xs = torch.from_numpy(ib).cuda(), torch.from_numpy(ism).cuda()
+    assert big.tile_levels > small.tile_levels
+    for _ in range(2):
+        assert np.array_equal(big.step(xb, steps=2).cpu().numpy(), ob.step(ib, steps=2))
+        assert np.array_equal(small.step(xs, steps=2).cpu().numpy(), osm.step(ism, steps=2))
+
+
 @pytest.mark.parametrize("steps", [0, 1, 2, 3, 4])
 def test_step_ping_pong_counts(P, steps):
     fam, r = W.VICSEK, 5
