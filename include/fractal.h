@@ -216,6 +216,42 @@ int fractal_batch_run(fractal_batch_t *b, void *stream);
 /* Cell updates and kernel launches of the last built run. */
 int fractal_batch_stats(const fractal_batch_t *b, int64_t *updates, int64_t *launches);
 
+/* ---- Serving: continuous batching of requests that arrive at any time ----
+ * (not in the paper).  A server owns a worker thread and a stream on the
+ * current device.  A request is (handle, seed and density of its Bernoulli
+ * initial state, steps, rule, result destination).  The worker admits queued
+ * requests in arrival order while their state (2 k^r bytes, stream-ordered
+ * allocation) fits the HBM budget, then repeatedly advances every resident
+ * request by up to `chunk` generations with one launch per group of
+ * requests sharing a fractal and tile depth, so requests that arrive while
+ * others run join the same launches.  A finished request's final state is
+ * copied to `host_out` (k^r bytes, pinned memory recommended; it must stay
+ * valid until the request is done) or, when host_out is NULL, reduced to its
+ * live-cell count.  Its latency is the time from submit to the moment the
+ * copy has landed.  The result equals fractal_step on the same initial state.
+ *   hbm_budget_bytes  admission budget (<= 0: 90% of the free memory now);
+ *                     a request needing more than the budget gets FR_EBUSY.
+ *   chunk             generations per tick (>= 1).
+ * Handles submitted to a server must outlive it and must not be re-planned
+ * (fractal_set_tile_levels, fractal_autotune) while it runs; the first submit
+ * of a handle builds its tables on the caller's thread. */
+typedef struct fractal_server fractal_server_t;
+int fractal_server_create(int64_t hbm_budget_bytes, int chunk, fractal_server_t **out);
+int fractal_server_destroy(fractal_server_t *srv);   /* finishes all requests first */
+int fractal_server_submit(fractal_server_t *srv, fractal_t *f, uint64_t seed, double p,
+                          int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
+                          uint8_t *host_out, int64_t *request_id);
+/* *done = 1 once the result has landed; then *latency_s = completion - submit
+ * and *population = live cells (host_out == NULL only), else -1.  Any pointer
+ * may be NULL.  FR_ENOTFOUND for an unknown id. */
+int fractal_server_poll(fractal_server_t *srv, int64_t request_id, int *done,
+                        double *latency_s, int64_t *population);
+/* Blocks until every submitted request is done (or the server failed). */
+int fractal_server_wait_all(fractal_server_t *srv);
+int fractal_server_stats(fractal_server_t *srv, int64_t *completed, int64_t *queued,
+                         int64_t *resident, int64_t *cell_updates, int64_t *launches,
+                         int64_t *hbm_used);
+
 /* Waits for `stream` and reports any asynchronous CUDA error. */
 int fractal_sync(void *stream);
 

@@ -11,7 +11,7 @@ Importing the package does not load the CUDA library; the first ``Fractal``
 does, and raises if ``libfractal.so`` has not been built.
 """
 
-__all__ = ["Fractal", "Batch", "FractalError", "build", "workloads"]
+__all__ = ["Fractal", "Batch", "Server", "FractalError", "build", "workloads"]
 
 
 def __getattr__(name):
@@ -21,6 +21,9 @@ def __getattr__(name):
     if name == "Batch":
         from .fractal import Batch
         return Batch
+    if name == "Server":
+        from .fractal import Server
+        return Server
     if name == "FractalError":
         from .capi import FractalError
         return FractalError

@@ -57,6 +57,12 @@ SIGNATURES = {
     "fractal_batch_clear": (c_int, [c_vp]),
     "fractal_batch_run": (c_int, [c_vp, c_vp]),
     "fractal_batch_stats": (c_int, [c_vp, c_i64p, c_i64p]),
+    "fractal_server_create": (c_int, [c_i64, c_int, ctypes.POINTER(c_vp)]),
+    "fractal_server_destroy": (c_int, [c_vp]),
+    "fractal_server_submit": (c_int, [c_vp, c_fp, c_u64, c_dbl, c_i64, c_u32, c_u32, c_vp, c_i64p]),
+    "fractal_server_poll": (c_int, [c_vp, c_i64, ctypes.POINTER(c_int), ctypes.POINTER(c_dbl), c_i64p]),
+    "fractal_server_wait_all": (c_int, [c_vp]),
+    "fractal_server_stats": (c_int, [c_vp, c_i64p, c_i64p, c_i64p, c_i64p, c_i64p, c_i64p]),
     "fractal_autotune": (c_int, [c_fp, c_vp, c_vp, c_u32, c_u32, c_vp, ctypes.POINTER(c_int)]),
 }
 

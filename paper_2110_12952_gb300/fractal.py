@@ -225,3 +225,57 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching request server (``fractal_server_*``)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, chunk: int = 8):
+        self._lib = capi.load()
+        h = ctypes.c_void_p()
+        capi.check(self._lib.fractal_server_create(int(hbm_budget_bytes), int(chunk), ctypes.byref(h)),
+                   self._lib)
+        self._h = h
+        self._keep = {}
+
+    def submit(self, fr: Fractal, seed: int, p: float, steps: int, rule=None,
+               host_out: torch.Tensor | None = None) -> int:
+        birth, survive = rule if rule is not None else fr.default_rule()
+        ptr = None
+        if host_out is not None:
+            if host_out.is_cuda or host_out.dtype != torch.uint8 or host_out.numel() != fr.cells:
+                raise TypeError("host_out must be a host uint8 tensor of k^r cells")
+            ptr = host_out.data_ptr()
+        rid = ctypes.c_int64()
+        capi.check(self._lib.fractal_server_submit(self._h, fr._h, seed & (2**64 - 1), float(p), int(steps),
+                                                   birth, survive, ptr, ctypes.byref(rid)), self._lib)
+        self._keep[rid.value] = (fr, host_out)
+        return rid.value
+
+    def poll(self, rid: int):
+        """(done, latency_s, population)."""
+        d, lat, pop = ctypes.c_int(), ctypes.c_double(), ctypes.c_int64()
+        capi.check(self._lib.fractal_server_poll(self._h, rid, ctypes.byref(d), ctypes.byref(lat),
+                                                 ctypes.byref(pop)), self._lib)
+        return bool(d.value), lat.value, pop.value
+
+    def wait_all(self):
+        capi.check(self._lib.fractal_server_wait_all(self._h), self._lib)
+
+    def stats(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(6)]
+        capi.check(self._lib.fractal_server_stats(self._h, *[ctypes.byref(x) for x in v]), self._lib)
+        keys = ["completed", "queued", "resident", "cell_updates", "launches", "hbm_used"]
+        return dict(zip(keys, (x.value for x in v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fractal_server_destroy(self._h)
+            self._h = None
+            self._keep = {}
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
