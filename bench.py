@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-plain-requests", type=int, default=600)
+    ap.add_argument("--serve-chunk", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile-levels", type=int, default=-1, help="tile depth L (-1: library choice)")
     return ap.parse_args()
@@ -69,7 +74,7 @@ def measured_peak():
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for name in ("step.cu", "internal.cuh", "handle.h"):
+    for name in ("step.cu", "step.h", "tma.cuh", "internal.cuh", "handle.h"):
         with open(os.path.join(ROOT, "paper_2110_12952_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -327,6 +332,9 @@ def run_ours(args, rank, world, dist):
     # many uneven instances: batched graph vs one instance per launch
     if not args.no_batch and rank == 0:
         extra["batched"] = batched_compare(args, W)
+    # open-loop Poisson requests: continuous-batching server vs one request at a time
+    if not args.no_serve and rank == 0:
+        extra["served"] = serve_compare(args, W)
 
     gpu_launches = args.steps  # one step-kernel launch per generation
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -444,6 +452,81 @@ def batched_compare(args, W):
         g.close()
     torch.cuda.empty_cache()
     return res
+
+
+def _pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if xs else None
+
+
+def serve_compare(args, W):
+    """Poisson arrivals (mean --serve-rate req/s for --serve-seconds, master
+    seed 8; family uniform over triangle/carpet/Vicsek, r uniform in the
+    batched ranges, generations log-uniform in [10, 1000], p ~ U[0.2, 0.6]),
+    results reduced to live-cell counts.  The server (continuous batching)
+    serves the whole trace; the plain path (one request at a time through
+    fractal_step on one stream, FIFO) serves its first --serve-plain-requests
+    requests."""
+    import torch
+    from paper_2110_12952_gb300 import Fractal, Server
+    trace = W.poisson_trace(rate_per_s=args.serve_rate, duration_s=args.serve_seconds, master_seed=8)
+    handles = {}
+    for q in trace:
+        key = (q.instance.family.name, q.instance.r)
+        if key not in handles:
+            handles[key] = Fractal.from_family(q.instance.family, q.instance.r)
+    for g in handles.values():     # tables and tile depth before the clock starts
+        x = g.init_bernoulli(1, 0.5)
+        g.autotune(x, torch.empty_like(x))
+        del x
+    torch.cuda.synchronize()
+    offered = sum(q.instance.cells * q.instance.steps for q in trace)
+    srv = Server(hbm_budget_bytes=0, chunk=args.serve_chunk)
+    ids = []
+    t0 = time.perf_counter()
+    t_srv0 = t0
+    for q in trace:
+        dt = t0 + q.arrival_s - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        i = q.instance
+        ids.append(srv.submit(handles[(i.family.name, i.r)], i.seed, i.p, i.steps))
+    srv.wait_all()
+    t_end = time.perf_counter()
+    lats = [srv.poll(rid)[1] for rid in ids]
+    st = srv.stats()
+    srv.close()
+    # plain path on the head of the same trace
+    head = trace[: args.serve_plain_requests]
+    plain = []
+    t0 = time.perf_counter()
+    for q in head:
+        dt = t0 + q.arrival_s - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        i = q.instance
+        g = handles[(i.family.name, i.r)]
+        x = g.init_bernoulli(i.seed, i.p)
+        y = g.step(x, steps=i.steps)
+        int(torch.count_nonzero(y).item())
+        plain.append(time.perf_counter() - (t0 + q.arrival_s))
+    plain_span = time.perf_counter() - t0
+    head_updates = sum(q.instance.cells * q.instance.steps for q in head)
+    for g in handles.values():
+        g.close()
+    torch.cuda.empty_cache()
+    served_span = t_end - t_srv0
+    return {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s "
+                        f"({len(trace)} requests), master seed 8, results reduced to live-cell counts",
+            "requests": len(trace), "offered_updates_per_s": offered / args.serve_seconds,
+            "served_updates": st["cell_updates"],
+            "served_span_s": served_span,
+            "served_updates_per_s": st["cell_updates"] / served_span,
+            "served_p50_s": _pct(lats, 50), "served_p99_s": _pct(lats, 99),
+            "served_mean_s": sum(lats) / len(lats), "served_launches": st["launches"],
+            "chunk": args.serve_chunk,
+            "plain_requests": len(head), "plain_p50_s": _pct(plain, 50), "plain_p99_s": _pct(plain, 99),
+            "plain_updates_per_s": head_updates / plain_span}
 
 
 def main():
