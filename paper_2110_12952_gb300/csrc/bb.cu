@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "step.h"
 
 namespace fr {
 
@@ -154,9 +155,167 @@ bb_kernel(BBArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
     }
 }
 
+// ---------------------------------------------------------------------
+// Vectorised path for 2D boxes with s = 2 and n a multiple of 512: each lane
+// owns 16 consecutive bytes of a row, a warp 512 columns; the warp walks down
+// a strip of rows with the rows above, at and below in registers (two more
+// rows' loads in flight).  Left/right neighbour bytes come from the adjacent
+// lanes (shuffles) or, at the warp's edges, from single-byte loads.  Counts
+// are byte-wise sums (<= 9, no carries); the rule is a byte look-up (prmt).
+
+struct BBFastArgs {
+    int32_t n;            // box side
+    int Lb;               // levels of the local bitmap (S = 2^Lb >= 32)
+    int32_t C;            // coarse side n / S
+    const uint32_t *local_bits, *coarse_bits;
+    int rows;             // rows per warp strip
+    int strips_x;         // n / 512
+    int64_t warps;        // strips_x * ceil(n / rows)
+    Rule rule;
+};
+
+__device__ __forceinline__ uint32_t prmt_bb(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// 4 bits -> 4 bytes of 0/1 (bit i lands in bit 8i; the other partial
+// products fall on distinct non-multiples of 8, so nothing carries)
+__device__ __forceinline__ uint32_t nib_bytes(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
+
+__device__ __forceinline__ uint32_t nz_bytes(uint32_t v)
+{
+    return (((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) >> 7 & 0x01010101u;
+}
+
+// membership bits of the 16 cells starting at x0 (a multiple of 16) in row y
+__device__ __forceinline__ uint32_t member16(const BBFastArgs &a, int32_t x0, int32_t y)
+{
+    const uint32_t S = 1u << a.Lb;
+    const uint32_t bit = ((uint32_t)y & (S - 1)) * S + ((uint32_t)x0 & (S - 1));
+    const uint32_t m = (__ldg(a.local_bits + (bit >> 5)) >> (bit & 31)) & 0xffffu;
+    const uint32_t c = (uint32_t)(y >> a.Lb) * (uint32_t)a.C + (uint32_t)(x0 >> a.Lb);
+    return ((__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u) ? m : 0u;
+}
+
+__device__ __forceinline__ uint32_t member1(const BBFastArgs &a, int32_t x, int32_t y)
+{
+    const uint32_t S = 1u << a.Lb;
+    const uint32_t bit = ((uint32_t)y & (S - 1)) * S + ((uint32_t)x & (S - 1));
+    const uint32_t c = (uint32_t)(y >> a.Lb) * (uint32_t)a.C + (uint32_t)(x >> a.Lb);
+    return (__ldg(a.local_bits + (bit >> 5)) >> (bit & 31)) & (__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u;
+}
+
+struct RowRaw {
+    uint4 v;
+    uint32_t el, er;   // raw bytes left of the warp's first cell / right of its last
+};
+
+__device__ __forceinline__ RowRaw load_row(const BBFastArgs &a, const uint8_t *__restrict__ in,
+                                           int32_t x0, int32_t y, int lane)
+{
+    RowRaw r;
+    r.v = make_uint4(0, 0, 0, 0);
+    r.el = r.er = 0;
+    if (y >= 0 && y < a.n) {
+        const uint8_t *row = in + (int64_t)y * a.n;
+        r.v = __ldg(reinterpret_cast<const uint4 *>(row + x0));
+        if (lane == 0 && x0 > 0) r.el = __ldg(row + x0 - 1);
+        if (lane == 31 && x0 + 16 < a.n) r.er = __ldg(row + x0 + 16);
+    }
+    return r;
+}
+
+// Masked 0/1 bytes, member bytes and horizontal 3-sums of one row.
+struct RowOut {
+    uint32_t d[4], m[4], h[4];
+};
+
+__device__ __forceinline__ void process_row(const BBFastArgs &a, const RowRaw &r, int32_t x0,
+                                            int32_t y, int lane, RowOut &o)
+{
+    uint32_t m16 = 0, ml = 0, mr = 0;
+    if (y >= 0 && y < a.n) {
+        m16 = member16(a, x0, y);
+        if (lane == 0 && x0 > 0) ml = member1(a, x0 - 1, y);
+        if (lane == 31 && x0 + 16 < a.n) mr = member1(a, x0 + 16, y);
+    }
+    const uint32_t raw[4] = {r.v.x, r.v.y, r.v.z, r.v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        o.m[q] = nib_bytes((m16 >> (4 * q)) & 0xfu);
+        o.d[q] = nz_bytes(raw[q]) & o.m[q];
+    }
+    uint32_t left = __shfl_up_sync(0xffffffffu, o.d[3], 1);    // byte 3 = cell x0 - 1
+    uint32_t right = __shfl_down_sync(0xffffffffu, o.d[0], 1); // byte 0 = cell x0 + 16
+    if (lane == 0) left = ((r.el != 0) & ml) << 24;
+    if (lane == 31) right = (r.er != 0) & mr;
+    const uint32_t w[6] = {left, o.d[0], o.d[1], o.d[2], o.d[3], right};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        o.h[q] = w[q + 1] + __funnelshift_l(w[q], w[q + 1], 8) + __funnelshift_r(w[q + 1], w[q + 2], 8);
+}
+
+__device__ __forceinline__ uint32_t rule4_bb(const uint32_t lut[4], uint32_t t, uint32_t alive)
+{
+    const uint32_t x = t | (t >> 4);
+    const uint32_t sel = prmt_bb(x, 0u, 0x3120u);
+    const uint32_t rd = prmt_bb(lut[0], lut[1], sel) & 0x01010101u;
+    const uint32_t rl = prmt_bb(lut[2], lut[3], sel) & 0x01010101u;
+    const uint32_t m = alive * 0xffu;
+    return (rl & m) | (rd & ~m);
+}
+
+__global__ void __launch_bounds__(128)
+bb_fast_kernel(BBFastArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wid >= a.warps) return;   // whole warps leave together
+    const int32_t x0 = (int32_t)(wid % a.strips_x) * 512 + lane * 16;
+    const int32_t y0 = (int32_t)(wid / a.strips_x) * a.rows;
+    const int32_t y1 = min(y0 + a.rows, a.n);
+    RowOut up, mid, dn;
+    process_row(a, load_row(a, in, x0, y0 - 1, lane), x0, y0 - 1, lane, up);
+    process_row(a, load_row(a, in, x0, y0, lane), x0, y0, lane, mid);
+    RowRaw r1 = load_row(a, in, x0, y0 + 1, lane);
+    RowRaw r2 = load_row(a, in, x0, y0 + 2, lane);
+    for (int32_t y = y0; y < y1; ++y) {
+        process_row(a, r1, x0, y + 1, lane, dn);
+        r1 = r2;
+        r2 = load_row(a, in, x0, y + 3, lane);
+        uint32_t nw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            nw[q] = rule4_bb(a.rule.lut, up.h[q] + mid.h[q] + dn.h[q], mid.d[q]) & mid.m[q];
+        *reinterpret_cast<uint4 *>(out + (int64_t)y * a.n + x0) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+        up = mid;
+        mid = dn;
+    }
+}
+
 int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                    uint32_t survive, cudaStream_t st)
 {
+    if (f->dim == 2 && f->s == 2 && f->side >= 512 && f->side % 512 == 0 && f->bb.Lb >= 5 &&
+        ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+        BBFastArgs a;
+        a.n = (int32_t)f->side;
+        a.Lb = f->bb.Lb;
+        a.C = f->bb.C;
+        a.local_bits = f->bb.local_bits;
+        a.coarse_bits = f->bb.coarse_bits;
+        a.rows = 64;
+        a.strips_x = a.n / 512;
+        a.warps = (int64_t)a.strips_x * ((a.n + a.rows - 1) / a.rows);
+        make_rule(birth, survive, &a.rule);
+        const int64_t grid = (a.warps + 3) / 4;
+        bb_fast_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
+        FR_CUDA(cudaGetLastError());
+        return FR_OK;
+    }
     const BBPlan &p = f->bb;
     BBArgs a;
     a.n = (int32_t)f->side;

@@ -214,6 +214,18 @@ def test_bb_exhaustive_with_garbage(P, fam, r):
         assert np.array_equal(out.cpu().numpy(), o.bb_step(box, rule=oracle_rule(fam), steps=steps))
 
 
+@pytest.mark.parametrize("fam,r", [(W.TRIANGLE, 10), (W.TRIANGLE_MIRRORED, 9), (W.FULL_SQUARE, 9)])
+def test_bb_vectorised_path_with_garbage(P, fam, r):
+    # s = 2 boxes of side >= 512 take the 16-bytes-per-lane path
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    rng = np.random.default_rng(r)
+    box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
+    b = torch.from_numpy(box).cuda()
+    for steps in (1, 2):
+        out = g.bb_step(b, steps=steps)
+        assert np.array_equal(out.cpu().numpy(), o.bb_step(box, steps=steps)), steps
+
+
 def test_scatter_gather_roundtrip(P):
     for fam, r in [(W.CARPET, 4), (W.MENGER, 3), (W.TRIANGLE, 9)]:
         g, o = gpu_fr(P, fam, r), ora(fam, r)
