@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-plain-requests", type=int, default=600)
@@ -329,6 +330,9 @@ def run_ours(args, rank, world, dist):
     # compact vs bounding box at equal r
     if not args.no_bb and rank == 0:
         extra["bb_compare"] = bb_compare(args, W)
+    # the other NBB fractals of the paper's Table 1 workloads
+    if not args.no_others and rank == 0:
+        extra["other_fractals"] = others_compare(args, W)
     # many uneven instances: batched graph vs one instance per launch
     if not args.no_batch and rank == 0:
         extra["batched"] = batched_compare(args, W)
@@ -452,6 +456,46 @@ def batched_compare(args, W):
         g.close()
     torch.cuda.empty_cache()
     return res
+
+
+def others_compare(args, W):
+    """Carpet r=10, Vicsek r=12, Menger r=6 (p 0.5, seeds 4-6; Menger B5/S45):
+    one generation per timed step after autotuning the tile depth; states
+    smaller than L2 are timed with an L2 flush before each generation.  The
+    carpet's and Menger's bounding boxes fit and are timed too."""
+    import torch
+    from paper_2110_12952_gb300 import Fractal
+    peak, _ = measured_peak()
+    flush_buf = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for inst in (W.CARPET_R10, W.VICSEK_R12, W.MENGER_R6):
+        g = Fractal.from_family(inst.family, inst.r)
+        x = g.init_bernoulli(inst.seed, inst.p)
+        y = torch.empty_like(x)
+        L = g.autotune(x, y)
+        small = 2 * g.cells < 4 * 129 * 2**20
+        n = max(5, min(args.steps, 20))
+        ct = time_steps(lambda: g.step(x, out=y, steps=1), n, 3,
+                        flush=(lambda: flush_buf.fill_(1)) if small else None)
+        ms = statistics.median(ct)
+        res = {"cells": g.cells, "tile_levels": L, "ms_per_generation": ms,
+               "updates_per_s": g.cells / (ms / 1e3), "hbm_frac": 2.0 * g.cells / (ms / 1e3) / 1e9 / peak,
+               "l2_flush": small}
+        if g.box_cells <= 4 * 2**30:
+            box = g.scatter(x)
+            del x, y
+            bo = torch.empty_like(box)
+            bt = time_steps(lambda: g.bb_step(box, out=bo, steps=1), max(3, n // 2), 2)
+            bms = statistics.median(bt)
+            res.update({"bb_box_cells": g.box_cells, "bb_ms_per_generation": bms,
+                        "bb_hbm_frac": 2.0 * g.box_cells / (bms / 1e3) / 1e9 / peak,
+                        "speedup_compact_vs_bb": bms / ms})
+            del box, bo
+        out[f"{inst.family.name}_r{inst.r}"] = res
+        g.close()
+        torch.cuda.empty_cache()
+    del flush_buf
+    return out
 
 
 def _pct(xs, q):
