@@ -65,6 +65,7 @@ struct StepArgs {
     int off_bar, off_box, off_tab, off_out, box_bytes;
     int ntab;              // entries of the shared table (cells or groups)
     int KG;                // cells per group (group / quad mode)
+    int tapz;              // tap mode: index of the all-zero group
     const uint32_t *tab;   // cell mode: box offset per cell; else window base per group
     const uint32_t *ring;
     const int32_t *nbr;
@@ -136,10 +137,147 @@ static int group_levels(const fractal *f)
     return 0;
 }
 
-enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9 };
+enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10 };
+
+// ---- tap mode: the Sierpinski triangle with offsets (0,0), (1,0), (0,1)
+// A level-2 group is 9 cells (lid 0..8 at (0,0) (1,0) (0,1) (2,0) (3,0)
+// (2,1) (0,2) (1,2) (0,3)) filling a 4x4 block.  The 6x6 window of a block
+// needs, besides its own cells, only 8 border cells ("taps") that are
+// members of a neighbouring block and touch a member of the block.  They
+// come from 6 neighbouring groups, in the order W, E, N, NE, S, SW.
+constexpr int kTapDirs = 6;
+constexpr int kTapDx[kTapDirs] = {-1, 1, 0, 1, 0, -1};
+constexpr int kTapDy[kTapDirs] = {0, 0, -1, -1, 1, 1};
+constexpr int kTaps = 8;
+// dir index, lid in that neighbour, window row, window column (0..5)
+constexpr int kTap[kTaps][4] = {{0, 4, 1, 0}, {1, 0, 1, 5}, {1, 2, 2, 5}, {2, 8, 0, 1},
+                                {3, 8, 0, 5}, {4, 0, 5, 1}, {4, 1, 5, 2}, {5, 4, 5, 0}};
+static const int32_t kTriangleOffsets[6] = {0, 0, 1, 0, 0, 1};
+
+static bool is_triangle(const fractal *f)
+{
+    if (f->dim != 2 || f->s != 2 || f->k != 3) return false;
+    for (int i = 0; i < 6; ++i)
+        if (f->offsets[i] != kTriangleOffsets[i]) return false;
+    return true;
+}
+
+// Tables of tap mode for tile depth L: per unit of 4 groups, the 6 neighbour
+// group indices of each group (uint16; halo groups continue after the
+// tile's NG groups, index NG + H is an all-zero group), and the halo bytes to
+// fetch per tile (ring entries: byte offset from the tile's first cell in the
+// stage | tile-table slot << 24, cell offset in the neighbouring tile).
+struct TapTables {
+    int NG = 0, NQ = 0, H = 0;
+    std::vector<uint32_t> words;   // NQ * 12
+    std::vector<uint32_t> ring;
+    bool ok = false;
+};
+
+static void host_lambda(const fractal *f, int64_t l, int L, int p[3]);
+static int64_t host_nu(const fractal *f, const int q[3], int L);
+
+static TapTables tap_tables(const fractal *f, int L)
+{
+    TapTables t;
+    if (!is_triangle(f) || L < 2) return t;
+    const int NB = 1 << (L - 2);            // blocks per side
+    int NG = 1;
+    for (int i = 0; i < L - 2; ++i) NG *= 3;
+    t.NG = NG;
+    t.NQ = (NG + 3) / 4;
+    std::vector<int> M((size_t)NB * NB, -1);
+    std::vector<int> bx(NG), by(NG);
+    for (int g = 0; g < NG; ++g) {
+        int c[3];
+        host_lambda(f, g, L - 2, c);
+        bx[g] = c[0];
+        by[g] = c[1];
+        M[(size_t)c[1] * NB + c[0]] = g;
+    }
+    // check the constant tap list against the fractal: every border cell of
+    // a window that is a member and touches a member of the block is a tap
+    {
+        int lid_of[4][4];
+        for (int y = 0; y < 4; ++y)
+            for (int x = 0; x < 4; ++x) {
+                int q[3] = {x, y, 0};
+                lid_of[y][x] = (int)host_nu(f, q, 2);
+            }
+        int found = 0;
+        for (int wr = 0; wr < 6; ++wr)
+            for (int wc = 0; wc < 6; ++wc) {
+                if (wr >= 1 && wr <= 4 && wc >= 1 && wc <= 4) continue;
+                const int x = wc - 1, y = wr - 1;
+                const int dx = x < 0 ? -1 : (x > 3 ? 1 : 0), dy = y < 0 ? -1 : (y > 3 ? 1 : 0);
+                const int lid = lid_of[(y + 4) % 4][(x + 4) % 4];
+                bool touch = false;
+                for (int ey = -1; ey <= 1; ++ey)
+                    for (int ex = -1; ex <= 1; ++ex) {
+                        const int ax = x + ex, ay = y + ey;
+                        if (ax >= 0 && ax < 4 && ay >= 0 && ay < 4 && lid_of[ay][ax] >= 0) touch = true;
+                    }
+                if (lid < 0 || !touch) continue;
+                bool listed = false;
+                for (int k = 0; k < kTaps; ++k)
+                    if (kTapDx[kTap[k][0]] == dx && kTapDy[kTap[k][0]] == dy && kTap[k][1] == lid &&
+                        kTap[k][2] == wr && kTap[k][3] == wc)
+                        listed = true;
+                if (!listed) return t;
+                ++found;
+            }
+        if (found != kTaps) return t;
+    }
+    // neighbour groups; halo slots for groups of neighbouring tiles
+    std::map<std::pair<int, int>, int> slot_of;   // (tile-table slot, group there) -> halo slot
+    std::vector<std::pair<int, int>> slots;
+    std::vector<int> nbr((size_t)t.NQ * 4 * kTapDirs, -2);
+    for (int g = 0; g < NG; ++g)
+        for (int d = 0; d < kTapDirs; ++d) {
+            int nx = bx[g] + kTapDx[d], ny = by[g] + kTapDy[d];
+            const int tdx = nx < 0 ? -1 : (nx >= NB ? 1 : 0), tdy = ny < 0 ? -1 : (ny >= NB ? 1 : 0);
+            nx = (nx + NB) % NB;
+            ny = (ny + NB) % NB;
+            const int gn = M[(size_t)ny * NB + nx];
+            int v = -2;                               // -2: the zero group
+            if (gn >= 0) {
+                if (tdx == 0 && tdy == 0) v = gn;
+                else {
+                    const int dir9 = (tdx + 1) + 3 * (tdy + 1);
+                    const int tslot = dir9 < 4 ? dir9 : dir9 - 1;
+                    auto key = std::make_pair(tslot, gn);
+                    auto it = slot_of.find(key);
+                    if (it == slot_of.end()) {
+                        it = slot_of.emplace(key, (int)slots.size()).first;
+                        slots.push_back(key);
+                    }
+                    v = -100 - it->second;            // halo slot, resolved below
+                }
+            }
+            nbr[(size_t)g * kTapDirs + d] = v;
+        }
+    t.H = (int)slots.size();
+    const int zero = NG + t.H;
+    if (zero >= 65536) return t;
+    t.words.assign((size_t)t.NQ * 12, 0);
+    for (int g = 0; g < t.NQ * 4; ++g)
+        for (int d = 0; d < kTapDirs; ++d) {
+            int v = g < NG ? nbr[(size_t)g * kTapDirs + d] : -2;
+            const uint32_t idx = (v == -2) ? (uint32_t)zero : (v <= -100 ? (uint32_t)(NG + (-100 - v)) : (uint32_t)v);
+            const int q = g / 4, u = g % 4, e = u * kTapDirs + d;   // 24 entries per unit
+            t.words[(size_t)q * 12 + e / 2] |= idx << (16 * (e % 2));
+        }
+    for (int hs = 0; hs < t.H; ++hs)
+        for (int lid = 0; lid < 9; ++lid) {
+            t.ring.push_back((uint32_t)(9 * (NG + hs) + lid) | ((uint32_t)slots[hs].first << 24));
+            t.ring.push_back((uint32_t)(9 * slots[hs].second + lid));
+        }
+    t.ok = true;
+    return t;
+}
 
 struct Geometry {
-    int mode, G, xoff;
+    int mode, G, xoff, halo;
     int64_t B, Px, Py, planes;
     int64_t box_bytes, tab_entries, block;
 };
@@ -159,6 +297,19 @@ static Geometry plan_geometry(const fractal *f, int L)
     g.xoff = 0;
     g.block = 256;
     const bool grp = g.G > 0 && L >= g.G && ipow(f->k, g.G) <= kMaxGroup;
+    g.halo = 0;
+    if (grp && is_triangle(f) && L >= 2 && (ipow(f->k, L - 2) + 3) / 4 <= 256) {
+        const TapTables t = tap_tables(f, L);
+        if (t.ok) {
+            g.mode = kModeTap;
+            g.Px = g.Py = g.planes = 0;
+            g.tab_entries = (int64_t)t.NQ * 12;
+            g.halo = t.H;
+            g.block = std::max<int64_t>(64, ((int64_t)t.NQ + 31) / 32 * 32);
+            g.box_bytes = 0;
+            return g;
+        }
+    }
     if (grp) {
         g.mode = (int)ipow(f->s, g.G);
         g.tab_entries = ipow(f->k, L - g.G);
@@ -200,8 +351,8 @@ static Layout plan_layout(const fractal *f, int L)
     Layout y;
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
-    y.nstage = (g.mode == kModeQuad) ? 2 : nstages();
-    y.tile_bytes = round16(KL + 64);
+    y.nstage = (g.mode == kModeQuad) ? 2 : (g.mode == kModeTap ? 3 : nstages());
+    y.tile_bytes = round16(KL + 64 + 9 * (g.halo + 1));
     y.stage_bytes = 4 * nbr_width(f->dim) + kStagePad + y.tile_bytes;
     int64_t off = y.nstage * y.stage_bytes;
     y.off_bar = off;
@@ -345,113 +496,121 @@ int ensure_step_plan(fractal *f)
         return FR_EINVAL;
     }
 
-    // local lambda -> padded box offset; occupancy of the interior
-    std::vector<uint32_t> pos(p.KL);
-    std::vector<uint8_t> occ((size_t)(geo.Px * geo.Py * geo.planes + 16), 0);
-    for (int64_t l = 0; l < p.KL; ++l) {
-        int c[3];
-        host_lambda(f, l, L, c);
-        int b[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
-        int64_t o = offset_of(b);
-        pos[l] = (uint32_t)o;
-        occ[o] = 1;
-    }
-    std::vector<uint32_t> tab;
-    if (p.mode != kModeCell) {
-        // group g = cells [g k^G, (g+1) k^G); its block sits at s^G * (coarse
-        // lambda of g over L - G levels); the window starts one cell up-left
-        const int KG = (int)ipow(f->k, p.G), SG = (int)ipow(f->s, p.G);
-        p.KG = KG;
-        for (int q = 0; q < kMaxGroup; ++q) p.lid_of_q[q] = -1;
-        for (int lid = 0; lid < KG; ++lid) {
-            int c[3];
-            host_lambda(f, lid, p.G, c);
-            p.lid_of_q[c[1] * SG + c[0]] = (int8_t)lid;
-            p.rel_of_lid[lid] = (int16_t)((c[1] + 1) * geo.Px + (c[0] + 1) + geo.xoff);
-        }
-        tab.resize(geo.tab_entries);
-        for (int64_t g = 0; g < geo.tab_entries; ++g) {
-            int c[3];
-            host_lambda(f, g, L - p.G, c);
-            tab[g] = (uint32_t)((int64_t)c[1] * SG * geo.Px + (int64_t)c[0] * SG);
-        }
-        if (p.mode == kModeQuad) {
-            // block row j <- group cells: first permute over words 0,1 of the
-            // group, then take cells 8..11 from word 2
-            for (int j = 0; j < 4; ++j) {
-                uint32_t sa = 0, sb = 0;
-                for (int c = 0; c < 4; ++c) {
-                    const int lid = p.lid_of_q[j * 4 + c];
-                    const uint32_t na = (lid >= 0 && lid < 8) ? (uint32_t)lid : kZeroSel;
-                    const uint32_t nb = (lid >= 8) ? (uint32_t)(4 + lid - 8) : (uint32_t)c;
-                    sa |= na << (4 * c);
-                    sb |= nb << (4 * c);
-                }
-                p.row_sel[2 * j] = sa;
-                p.row_sel[2 * j + 1] = sb;
-            }
-            // cell order word m <- block sums (16 bytes: row j, column c at 4j+c)
-            for (int m = 0; m < 3; ++m) {
-                uint32_t sa = 0, sb = 0, sc = 0;
-                for (int i = 0; i < 4; ++i) {
-                    const int lid = 4 * m + i;
-                    uint32_t na = kZeroSel, nb = kZeroSel, nc = kZeroSel;
-                    if (lid < KG) {
-                        int c[3];
-                        host_lambda(f, lid, p.G, c);
-                        const int idx = 4 * c[1] + c[0];
-                        if (idx < 8) { na = idx; nc = i; }
-                        else { nb = idx - 8; nc = 4 + i; }
-                    }
-                    sa |= na << (4 * i);
-                    sb |= nb << (4 * i);
-                    sc |= nc << (4 * i);
-                }
-                p.pack_sel[3 * m] = sa;
-                p.pack_sel[3 * m + 1] = sb;
-                p.pack_sel[3 * m + 2] = sc;
-            }
-        }
+    std::vector<uint32_t> tab, ring;
+    if (p.mode == kModeTap) {
+        const TapTables t = tap_tables(f, L);
+        p.KG = 9;
+        p.tapz = t.NG + t.H;
+        tab = t.words;
+        ring = t.ring;
     } else {
-        tab = pos;
-    }
-    // halo ring: padded cells with some coordinate 0 or B+1 that are members
-    // of their (wrapped) local box and touch an interior member
-    std::vector<uint32_t> ring;
-    const int centre = (dim == 3) ? 13 : 4;
-    for (int64_t bz = 0; bz < W[2]; ++bz)
-        for (int64_t by = 0; by < W[1]; ++by)
-            for (int64_t bx = 0; bx < W[0]; ++bx) {
-                int b[3] = {(int)bx, (int)by, (int)bz};
-                bool halo = false;
-                int dir = 0, m3 = 1, q[3] = {0, 0, 0};
-                for (int i = 0; i < dim; ++i) {
-                    int d = (b[i] == 0) ? -1 : (b[i] == W[i] - 1 ? 1 : 0);
-                    if (d) halo = true;
-                    dir += (d + 1) * m3;
-                    m3 *= 3;
-                    q[i] = (b[i] == 0) ? p.B - 1 : (b[i] == W[i] - 1 ? 0 : b[i] - 1);
-                }
-                if (!halo) continue;
-                int64_t lw = host_nu(f, q, L);
-                if (lw < 0) continue;
-                bool touches = false;
-                const int nq = (dim == 3) ? 27 : 9;
-                for (int e = 0; e < nq && !touches; ++e) {
-                    int dd[3] = {e % 3 - 1, (e / 3) % 3 - 1, e / 9 - 1};
-                    int nb[3] = {0, 0, 0};
-                    bool inside = true;
-                    for (int i = 0; i < dim; ++i) {
-                        nb[i] = b[i] + dd[i];
-                        if (nb[i] < 1 || nb[i] > W[i] - 2) inside = false;
-                    }
-                    if (inside && occ[offset_of(nb)]) touches = true;
-                }
-                if (!touches) continue;
-                const int slot = dir < centre ? dir : dir - 1;
-                ring.push_back((uint32_t)offset_of(b) | ((uint32_t)slot << 24));
-                ring.push_back((uint32_t)lw);
+        // local lambda -> padded box offset; occupancy of the interior
+        std::vector<uint32_t> pos(p.KL);
+        std::vector<uint8_t> occ((size_t)(geo.Px * geo.Py * geo.planes + 16), 0);
+        for (int64_t l = 0; l < p.KL; ++l) {
+            int c[3];
+            host_lambda(f, l, L, c);
+            int b[3] = {c[0] + 1, c[1] + 1, c[2] + 1};
+            int64_t o = offset_of(b);
+            pos[l] = (uint32_t)o;
+            occ[o] = 1;
+        }
+        if (p.mode != kModeCell) {
+            // group g = cells [g k^G, (g+1) k^G); its block sits at s^G * (coarse
+            // lambda of g over L - G levels); the window starts one cell up-left
+            const int KG = (int)ipow(f->k, p.G), SG = (int)ipow(f->s, p.G);
+            p.KG = KG;
+            for (int q = 0; q < kMaxGroup; ++q) p.lid_of_q[q] = -1;
+            for (int lid = 0; lid < KG; ++lid) {
+                int c[3];
+                host_lambda(f, lid, p.G, c);
+                p.lid_of_q[c[1] * SG + c[0]] = (int8_t)lid;
+                p.rel_of_lid[lid] = (int16_t)((c[1] + 1) * geo.Px + (c[0] + 1) + geo.xoff);
             }
+            tab.resize(geo.tab_entries);
+            for (int64_t g = 0; g < geo.tab_entries; ++g) {
+                int c[3];
+                host_lambda(f, g, L - p.G, c);
+                tab[g] = (uint32_t)((int64_t)c[1] * SG * geo.Px + (int64_t)c[0] * SG);
+            }
+            if (p.mode == kModeQuad) {
+                // block row j <- group cells: first permute over words 0,1 of the
+                // group, then take cells 8..11 from word 2
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t sa = 0, sb = 0;
+                    for (int c = 0; c < 4; ++c) {
+                        const int lid = p.lid_of_q[j * 4 + c];
+                        const uint32_t na = (lid >= 0 && lid < 8) ? (uint32_t)lid : kZeroSel;
+                        const uint32_t nb = (lid >= 8) ? (uint32_t)(4 + lid - 8) : (uint32_t)c;
+                        sa |= na << (4 * c);
+                        sb |= nb << (4 * c);
+                    }
+                    p.row_sel[2 * j] = sa;
+                    p.row_sel[2 * j + 1] = sb;
+                }
+                // cell order word m <- block sums (16 bytes: row j, column c at 4j+c)
+                for (int m = 0; m < 3; ++m) {
+                    uint32_t sa = 0, sb = 0, sc = 0;
+                    for (int i = 0; i < 4; ++i) {
+                        const int lid = 4 * m + i;
+                        uint32_t na = kZeroSel, nb = kZeroSel, nc = kZeroSel;
+                        if (lid < KG) {
+                            int c[3];
+                            host_lambda(f, lid, p.G, c);
+                            const int idx = 4 * c[1] + c[0];
+                            if (idx < 8) { na = idx; nc = i; }
+                            else { nb = idx - 8; nc = 4 + i; }
+                        }
+                        sa |= na << (4 * i);
+                        sb |= nb << (4 * i);
+                        sc |= nc << (4 * i);
+                    }
+                    p.pack_sel[3 * m] = sa;
+                    p.pack_sel[3 * m + 1] = sb;
+                    p.pack_sel[3 * m + 2] = sc;
+                }
+            }
+        } else {
+            tab = pos;
+        }
+        // halo ring: padded cells with some coordinate 0 or B+1 that are members
+        // of their (wrapped) local box and touch an interior member
+        const int centre = (dim == 3) ? 13 : 4;
+        for (int64_t bz = 0; bz < W[2]; ++bz)
+            for (int64_t by = 0; by < W[1]; ++by)
+                for (int64_t bx = 0; bx < W[0]; ++bx) {
+                    int b[3] = {(int)bx, (int)by, (int)bz};
+                    bool halo = false;
+                    int dir = 0, m3 = 1, q[3] = {0, 0, 0};
+                    for (int i = 0; i < dim; ++i) {
+                        int d = (b[i] == 0) ? -1 : (b[i] == W[i] - 1 ? 1 : 0);
+                        if (d) halo = true;
+                        dir += (d + 1) * m3;
+                        m3 *= 3;
+                        q[i] = (b[i] == 0) ? p.B - 1 : (b[i] == W[i] - 1 ? 0 : b[i] - 1);
+                    }
+                    if (!halo) continue;
+                    int64_t lw = host_nu(f, q, L);
+                    if (lw < 0) continue;
+                    bool touches = false;
+                    const int nq = (dim == 3) ? 27 : 9;
+                    for (int e = 0; e < nq && !touches; ++e) {
+                        int dd[3] = {e % 3 - 1, (e / 3) % 3 - 1, e / 9 - 1};
+                        int nb[3] = {0, 0, 0};
+                        bool inside = true;
+                        for (int i = 0; i < dim; ++i) {
+                            nb[i] = b[i] + dd[i];
+                            if (nb[i] < 1 || nb[i] > W[i] - 2) inside = false;
+                        }
+                        if (inside && occ[offset_of(nb)]) touches = true;
+                    }
+                    if (!touches) continue;
+                    const int slot = dir < centre ? dir : dir - 1;
+                    ring.push_back((uint32_t)offset_of(b) | ((uint32_t)slot << 24));
+                    ring.push_back((uint32_t)lw);
+                }
+
+    }
     p.nring = (int)(ring.size() / 2);
     FR_CUDA(cudaMalloc(&p.pos, tab.size() * sizeof(uint32_t)));
     FR_CUDA(cudaMemcpy(p.pos, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -474,6 +633,7 @@ int ensure_step_plan(fractal *f)
     }
     if (dim == 3) rc = configure<3, kModeCell>(p, f->num_sms);
     else if (p.mode == kModeQuad) rc = configure<2, kModeQuad>(p, f->num_sms);
+    else if (p.mode == kModeTap) rc = configure<2, kModeTap>(p, f->num_sms);
     else if (p.mode == kModeGroup4) rc = configure<2, kModeGroup4>(p, f->num_sms);
     else if (p.mode == kModeGroup3) rc = configure<2, kModeGroup3>(p, f->num_sms);
     else rc = configure<2, kModeCell>(p, f->num_sms);
@@ -578,6 +738,7 @@ struct TileIO {
 template <int DIM>
 struct CellPolicy {
     static constexpr int NDIR = (DIM == 3) ? 27 : 9;
+    static constexpr bool kRingInTile = false;  // halo bytes go to the box
     struct Regs { int nb[NDIR - 1]; };
     __device__ static void init(const StepArgs &a, Regs &R)
     {
@@ -614,6 +775,7 @@ struct CellPolicy {
 template <int SG>
 struct GroupPolicy {
     struct Regs {};
+    static constexpr bool kRingInTile = false;  // halo bytes go to the box
     __device__ static void init(const StepArgs &, Regs &) {}
     __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *box,
                                    const uint32_t *tab, Regs &)
@@ -647,6 +809,7 @@ struct GroupPolicy {
 // never touch the box.
 struct QuadPolicy {
     static constexpr int KG = kQuadKG;
+    static constexpr bool kRingInTile = false;  // halo bytes go to the box
     struct Regs {
         uint32_t v[KG + 1];     // the unit's 36 input bytes as words (v[KG] = 0)
         uint32_t rw[4][4];      // block rows of the four groups
@@ -753,6 +916,134 @@ struct QuadPolicy {
     }
 };
 
+// ---- tap policy (the triangle; see kTap): no box.  A thread owns 4
+// consecutive groups (36 cells); it reads its cells and the 8 taps of each
+// group straight from the stage, where the halo groups follow the tile's own
+// groups, and writes 9 output words.
+struct TapPolicy {
+    static constexpr bool kRingInTile = true;   // halo bytes go after the tile's bytes
+    static constexpr int KG = 9;
+    struct Regs {};
+    __device__ static void init(const StepArgs &, Regs &) {}
+
+    __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *, const uint32_t *, Regs &)
+    {
+        // the all-zero group (after the halo groups; the bulk copy may have
+        // written there)
+        if (threadIdx.x < KG) const_cast<uint8_t *>(io.data)[io.a_in + KG * a.tapz + threadIdx.x] = 0;
+    }
+
+    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *, const uint32_t *tab,
+                                   Regs &)
+    {
+        const int q = threadIdx.x;
+        const int nq = a.ntab / 12;
+        if (q >= nq) return;
+        const uint8_t *tin = io.data + io.a_in;
+        const int off = io.a_in + 36 * q;
+        const uint8_t *wp = io.data + (off & ~3);
+        const uint32_t sh = (uint32_t)(off & 3) * 8u;
+        uint32_t v[KG + 1];
+        {
+            uint32_t w[KG + 1];
+#pragma unroll
+            for (int i = 0; i <= KG; ++i) w[i] = lds32(wp + 4 * i);
+            uint32_t any = 0;
+#pragma unroll
+            for (int i = 0; i < KG; ++i) {
+                v[i] = __funnelshift_r(w[i], w[i + 1], sh);
+                any |= v[i];
+            }
+            v[KG] = 0;
+            if (any & 0xfefefefeu) {
+#pragma unroll
+                for (int i = 0; i < KG; ++i) v[i] = bytes_to_01(v[i]);
+            }
+        }
+        // neighbour group indices of the unit's 4 groups (uint16, W E N NE S SW)
+        const uint4 *tq = reinterpret_cast<const uint4 *>(tab + 12 * q);
+        const uint4 n0 = tq[0], n1 = tq[1], n2 = tq[2];
+        const uint32_t nw[12] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w};
+        uint32_t T[KG + 1];
+#pragma unroll
+        for (int i = 0; i <= KG; ++i) T[i] = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b0 = KG * u;
+            const uint32_t g0w = __funnelshift_r(v[b0 / 4], v[b0 / 4 + 1], (b0 % 4) * 8);
+            const uint32_t g1w = __funnelshift_r(v[b0 / 4 + 1], v[b0 / 4 + 2], (b0 % 4) * 8);
+            const uint32_t g2w = __funnelshift_r(v[b0 / 4 + 2], v[b0 / 4 + 3 <= KG ? b0 / 4 + 3 : KG], (b0 % 4) * 8);
+            // block rows (cells x = 0..3): lids 0 1 3 4 / 2 - 5 - / 6 7 - - / 8 - - -
+            const uint32_t rw0 = prmt(g0w, g1w, 0x4310u);
+            const uint32_t rw1 = prmt(g0w, g1w, 0x8582u);
+            const uint32_t rw2 = prmt(g1w, 0u, 0x8832u);
+            const uint32_t rw3 = g2w & 0xffu;
+            // the 8 taps
+            const uint8_t *nb[kTapDirs];
+#pragma unroll
+            for (int d = 0; d < kTapDirs; ++d) {
+                const int e = u * kTapDirs + d;
+                nb[d] = tin + KG * ((nw[e / 2] >> (16 * (e % 2))) & 0xffffu);
+            }
+            const uint32_t tW4 = nb[0][4], tE0 = nb[1][0], tE2 = nb[1][2], tN8 = nb[2][8];
+            const uint32_t tNE8 = nb[3][8], tS0 = nb[4][0], tS1 = nb[4][1], tSW4 = nb[5][4];
+            // window rows: bytes 0..3 in lo, 4..5 in hi (columns x = -1..4)
+            uint32_t lo[6], hi[6];
+            lo[0] = tN8 << 8;
+            hi[0] = tNE8 << 8;
+            lo[1] = (rw0 << 8) | tW4;
+            hi[1] = (rw0 >> 24) | (tE0 << 8);
+            lo[2] = rw1 << 8;
+            hi[2] = (rw1 >> 24) | (tE2 << 8);
+            lo[3] = rw2 << 8;
+            hi[3] = rw2 >> 24;
+            lo[4] = rw3 << 8;
+            hi[4] = 0;
+            lo[5] = tSW4 | (tS0 << 8) | (tS1 << 16);
+            hi[5] = 0;
+            const uint32_t pl01 = lo[0] + lo[1], pl23 = lo[2] + lo[3], pl45 = lo[4] + lo[5];
+            const uint32_t ph01 = hi[0] + hi[1], ph23 = hi[2] + hi[3], ph45 = hi[4] + hi[5];
+            const uint32_t vl[4] = {pl01 + lo[2], lo[1] + pl23, pl23 + lo[4], lo[3] + pl45};
+            const uint32_t vh[4] = {ph01 + hi[2], hi[1] + ph23, ph23 + hi[4], hi[3] + ph45};
+            uint32_t S[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                S[j] = vl[j] + __funnelshift_r(vl[j], vh[j], 8) + __funnelshift_r(vl[j], vh[j], 16);
+            // sums in lid order: block positions 0 1 4 2 | 3 6 8 9 | 12
+            const uint32_t tg0 = prmt(S[0], S[1], 0x2410u);
+            const uint32_t tg1 = prmt(prmt(S[0], S[1], 0x8863u), S[2], 0x5410u);
+            const uint32_t tg2 = S[3] & 0xffu;
+            const uint32_t tg[3] = {tg0, tg1, tg2};
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const int b = b0 + 4 * m;
+                if (b / 4 <= KG) {
+                    T[b / 4] |= tg[m] << ((b % 4) * 8);
+                    if ((b % 4) && b / 4 + 1 <= KG) T[b / 4 + 1] |= tg[m] >> (32 - (b % 4) * 8);
+                }
+            }
+        }
+        uint32_t o[KG];
+#pragma unroll
+        for (int i = 0; i < KG; ++i) o[i] = rule4(io.rule.lut, T[i], v[i]);
+        // output bytes [36q, 36q + 36) of the tile; words straddling the
+        // neighbouring units' bytes are written byte by byte
+        uint8_t *ob = io.ostage + io.a_out + 36 * q;
+        const int m = (io.a_out + 36 * q) & 3;
+        if (m == 0) {
+#pragma unroll
+            for (int i = 0; i < KG; ++i) sts32(ob + 4 * i, o[i]);
+        } else {
+            uint8_t *al = ob - m + 4;            // first whole word
+            const uint32_t sl = 8u * (uint32_t)(4 - m);
+#pragma unroll
+            for (int i = 0; i < KG - 1; ++i) sts32(al + 4 * i, __funnelshift_r(o[i], o[i + 1], sl));
+            for (int j = 0; j < 4 - m; ++j) ob[j] = (uint8_t)(o[0] >> (8 * j));
+            for (int j = 0; j < m; ++j) ob[36 - m + j] = (uint8_t)(o[KG - 1] >> (8 * (4 - m + j)));
+        }
+    }
+};
+
 template <int DIM, int MODE>
 struct PolicyOf;
 template <int DIM>
@@ -763,6 +1054,8 @@ template <>
 struct PolicyOf<2, kModeGroup4> { using type = GroupPolicy<4>; };
 template <>
 struct PolicyOf<2, kModeQuad> { using type = QuadPolicy; };
+template <>
+struct PolicyOf<2, kModeTap> { using type = TapPolicy; };
 
 // A tile of the launch resolved to its instance's buffers, table and rule.
 struct TileRef {
@@ -902,6 +1195,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         tile_rule<MULTI>(a, Tg, io.rule);
 
         Pol::scatter(a, io, box, tab, R);
+        uint8_t *rdst = Pol::kRingInTile ? data + io.a_in : box;
         // halo cells: the first kRingRegs per thread were prefetched during the
         // previous tile (when `pref`), the rest are loaded now
 #pragma unroll
@@ -914,7 +1208,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
                     const int32_t tn = nrow[w0 >> 24];
                     v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
                 }
-                box[w0 & 0xffffff] = v != 0;
+                rdst[w0 & 0xffffff] = v != 0;
             }
         }
         for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
@@ -922,7 +1216,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
             const int32_t tn = nrow[w0 >> 24];
             uint8_t v = 0;
             if (tn >= 0) v = t.in[(int64_t)tn * a.KL + lw] != 0;
-            box[w0 & 0xffffff] = v;
+            rdst[w0 & 0xffffff] = v;
         }
         // prefetch the next tile's halo values when its stage has already
         // landed (never wait for it here); the loads stay in flight while
@@ -948,14 +1242,21 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         }
         if (tid == 0) bulk_wait_read_all();   // previous tile's bulk store has read ostage
         __syncthreads();
-        // stage s is consumed: refill it with the tile nstage iterations ahead
-        if (tid == 0) {
+        // stage s is consumed (policies that compute from the stage itself
+        // refill it after the compute): refill it with the tile nstage
+        // iterations ahead
+        if (!Pol::kRingInTile && tid == 0) {
             const int64_t Tn = Tg + a.nstage * G;
             fence_proxy_async_smem();
             if (Tn < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tn), stage, &bars[s]);
         }
         Pol::compute(a, io, box, tab, R);
         __syncthreads();
+        if (Pol::kRingInTile && tid == 0) {
+            const int64_t Tn = Tg + a.nstage * G;
+            fence_proxy_async_smem();
+            if (Tn < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tn), stage, &bars[s]);
+        }
         uint8_t *tout = ostage + io.a_out;
         const uintptr_t c0 = (ostart + 15) & ~(uintptr_t)15;
         const uintptr_t c1 = oend & ~(uintptr_t)15;
@@ -1028,6 +1329,7 @@ static void fill_args(const fractal *f, StepArgs &a)
     a.box_bytes = p.box_bytes;
     a.ntab = p.ntab;
     a.KG = p.KG;
+    a.tapz = p.tapz;
     a.tab = p.pos;
     a.ring = p.ring;
     a.nbr = p.nbr;
@@ -1052,6 +1354,8 @@ static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t
         step_tma_kernel<3, kModeCell, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeQuad)
         step_tma_kernel<2, kModeQuad, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (p.mode == kModeTap)
+        step_tma_kernel<2, kModeTap, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup4)
         step_tma_kernel<2, kModeGroup4, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup3)

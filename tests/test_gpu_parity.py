@@ -145,6 +145,18 @@ def test_step_exhaustive_all_tile_depths(P, fam, r, levels):
         assert np.array_equal(out.cpu().numpy(), ref), f"L={L}"
 
 
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 7, 8])
+def test_triangle_many_tiles_per_cta(P, L):
+    # r = 14 gives thousands of tiles at every depth, so each CTA reuses its
+    # pipeline stages many times
+    fam, r = W.TRIANGLE, 14
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(8, 0.4)
+    x = torch.from_numpy(init).cuda()
+    g.tile_levels = L
+    assert np.array_equal(g.step(x, steps=2).cpu().numpy(), o.step(init, steps=2)), f"L={L}"
+
+
 def test_autotune_keeps_parity(P):
     fam, r = W.TRIANGLE, 11
     g, o = gpu_fr(P, fam, r), ora(fam, r)
