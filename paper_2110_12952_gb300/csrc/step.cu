@@ -146,6 +146,7 @@ enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap 
 // members of a neighbouring block and touch a member of the block.  They
 // come from 6 neighbouring groups, in the order W, E, N, NE, S, SW.
 constexpr int kTapDirs = 6;
+constexpr int kTapUnit = 8;    // groups per thread
 constexpr int kTapDx[kTapDirs] = {-1, 1, 0, 1, 0, -1};
 constexpr int kTapDy[kTapDirs] = {0, 0, -1, -1, 1, 1};
 constexpr int kTaps = 8;
@@ -185,7 +186,7 @@ static TapTables tap_tables(const fractal *f, int L)
     int NG = 1;
     for (int i = 0; i < L - 2; ++i) NG *= 3;
     t.NG = NG;
-    t.NQ = (NG + 3) / 4;
+    t.NQ = (NG + kTapUnit - 1) / kTapUnit;
     std::vector<int> M((size_t)NB * NB, -1);
     std::vector<int> bx(NG), by(NG);
     for (int g = 0; g < NG; ++g) {
@@ -231,7 +232,7 @@ static TapTables tap_tables(const fractal *f, int L)
     // neighbour groups; halo slots for groups of neighbouring tiles
     std::map<std::pair<int, int>, int> slot_of;   // (tile-table slot, group there) -> halo slot
     std::vector<std::pair<int, int>> slots;
-    std::vector<int> nbr((size_t)t.NQ * 4 * kTapDirs, -2);
+    std::vector<int> nbr((size_t)t.NQ * kTapUnit * kTapDirs, -2);
     for (int g = 0; g < NG; ++g)
         for (int d = 0; d < kTapDirs; ++d) {
             int nx = bx[g] + kTapDx[d], ny = by[g] + kTapDy[d];
@@ -259,13 +260,13 @@ static TapTables tap_tables(const fractal *f, int L)
     t.H = (int)slots.size();
     const int zero = NG + t.H;
     if (zero >= 65536) return t;
-    t.words.assign((size_t)t.NQ * 12, 0);
-    for (int g = 0; g < t.NQ * 4; ++g)
+    // 3 words per group (6 uint16: W E | N NE | S SW), groups in order
+    t.words.assign((size_t)t.NQ * kTapUnit * 3, 0);
+    for (int g = 0; g < t.NQ * kTapUnit; ++g)
         for (int d = 0; d < kTapDirs; ++d) {
             int v = g < NG ? nbr[(size_t)g * kTapDirs + d] : -2;
             const uint32_t idx = (v == -2) ? (uint32_t)zero : (v <= -100 ? (uint32_t)(NG + (-100 - v)) : (uint32_t)v);
-            const int q = g / 4, u = g % 4, e = u * kTapDirs + d;   // 24 entries per unit
-            t.words[(size_t)q * 12 + e / 2] |= idx << (16 * (e % 2));
+            t.words[(size_t)g * 3 + d / 2] |= idx << (16 * (d % 2));
         }
     for (int hs = 0; hs < t.H; ++hs)
         for (int lid = 0; lid < 9; ++lid) {
@@ -298,12 +299,12 @@ static Geometry plan_geometry(const fractal *f, int L)
     g.block = 256;
     const bool grp = g.G > 0 && L >= g.G && ipow(f->k, g.G) <= kMaxGroup;
     g.halo = 0;
-    if (grp && is_triangle(f) && L >= 2 && (ipow(f->k, L - 2) + 3) / 4 <= 256) {
+    if (grp && is_triangle(f) && L >= 2 && (ipow(f->k, L - 2) + kTapUnit - 1) / kTapUnit <= 256) {
         const TapTables t = tap_tables(f, L);
         if (t.ok) {
             g.mode = kModeTap;
             g.Px = g.Py = g.planes = 0;
-            g.tab_entries = (int64_t)t.NQ * 12;
+            g.tab_entries = (int64_t)t.NQ * kTapUnit * 3;
             g.halo = t.H;
             g.block = std::max<int64_t>(64, ((int64_t)t.NQ + 31) / 32 * 32);
             g.box_bytes = 0;
@@ -352,7 +353,9 @@ static Layout plan_layout(const fractal *f, int L)
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
     y.nstage = (g.mode == kModeQuad) ? 2 : (g.mode == kModeTap ? 3 : nstages());
-    y.tile_bytes = round16(KL + 64 + 9 * (g.halo + 1));
+    // slack: 16-byte rounding of the bulk copy, halo and zero groups, and
+    // the tap units' whole-word reads and writes past the tile's last cell
+    y.tile_bytes = round16(KL + 64 + 9 * (g.halo + 1) + 9 * kTapUnit);
     y.stage_bytes = 4 * nbr_width(f->dim) + kStagePad + y.tile_bytes;
     int64_t off = y.nstage * y.stage_bytes;
     y.off_bar = off;
@@ -916,13 +919,15 @@ struct QuadPolicy {
     }
 };
 
-// ---- tap policy (the triangle; see kTap): no box.  A thread owns 4
-// consecutive groups (36 cells); it reads its cells and the 8 taps of each
+// ---- tap policy (the triangle; see kTap): no box.  A thread owns U
+// consecutive groups (9U cells); it reads its cells and the 8 taps of each
 // group straight from the stage, where the halo groups follow the tile's own
-// groups, and writes 9 output words.
+// groups, and writes 9U/4 output words.
+template <int U>
 struct TapPolicy {
     static constexpr bool kRingInTile = true;   // halo bytes go after the tile's bytes
     static constexpr int KG = 9;
+    static constexpr int NW = KG * U / 4;       // words per unit
     struct Regs {};
     __device__ static void init(const StepArgs &, Regs &) {}
 
@@ -937,109 +942,95 @@ struct TapPolicy {
                                    Regs &)
     {
         const int q = threadIdx.x;
-        const int nq = a.ntab / 12;
+        const int nq = a.ntab / (3 * U);
         if (q >= nq) return;
         const uint8_t *tin = io.data + io.a_in;
-        const int off = io.a_in + 36 * q;
+        const int off = io.a_in + 9 * U * q;
         const uint8_t *wp = io.data + (off & ~3);
         const uint32_t sh = (uint32_t)(off & 3) * 8u;
-        uint32_t v[KG + 1];
+        uint32_t v[NW + 1];
         {
-            uint32_t w[KG + 1];
+            uint32_t w[NW + 1];
 #pragma unroll
-            for (int i = 0; i <= KG; ++i) w[i] = lds32(wp + 4 * i);
+            for (int i = 0; i <= NW; ++i) w[i] = lds32(wp + 4 * i);
             uint32_t any = 0;
 #pragma unroll
-            for (int i = 0; i < KG; ++i) {
+            for (int i = 0; i < NW; ++i) {
                 v[i] = __funnelshift_r(w[i], w[i + 1], sh);
                 any |= v[i];
             }
-            v[KG] = 0;
+            v[NW] = 0;
             if (any & 0xfefefefeu) {
 #pragma unroll
-                for (int i = 0; i < KG; ++i) v[i] = bytes_to_01(v[i]);
+                for (int i = 0; i < NW; ++i) v[i] = bytes_to_01(v[i]);
             }
         }
-        // neighbour group indices of the unit's 4 groups (uint16, W E N NE S SW)
-        const uint4 *tq = reinterpret_cast<const uint4 *>(tab + 12 * q);
-        const uint4 n0 = tq[0], n1 = tq[1], n2 = tq[2];
-        const uint32_t nw[12] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w};
-        uint32_t T[KG + 1];
+        uint32_t T[NW + 1];
 #pragma unroll
-        for (int i = 0; i <= KG; ++i) T[i] = 0;
+        for (int i = 0; i <= NW; ++i) T[i] = 0;
+        const uint32_t *tq = tab + 3 * U * q;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int b0 = KG * u;
             const uint32_t g0w = __funnelshift_r(v[b0 / 4], v[b0 / 4 + 1], (b0 % 4) * 8);
             const uint32_t g1w = __funnelshift_r(v[b0 / 4 + 1], v[b0 / 4 + 2], (b0 % 4) * 8);
-            const uint32_t g2w = __funnelshift_r(v[b0 / 4 + 2], v[b0 / 4 + 3 <= KG ? b0 / 4 + 3 : KG], (b0 % 4) * 8);
+            const uint32_t g2w = __funnelshift_r(v[b0 / 4 + 2], v[b0 / 4 + 3 <= NW ? b0 / 4 + 3 : NW], (b0 % 4) * 8);
             // block rows (cells x = 0..3): lids 0 1 3 4 / 2 - 5 - / 6 7 - - / 8 - - -
             const uint32_t rw0 = prmt(g0w, g1w, 0x4310u);
             const uint32_t rw1 = prmt(g0w, g1w, 0x8582u);
             const uint32_t rw2 = prmt(g1w, 0u, 0x8832u);
             const uint32_t rw3 = g2w & 0xffu;
-            // the 8 taps
-            const uint8_t *nb[kTapDirs];
-#pragma unroll
-            for (int d = 0; d < kTapDirs; ++d) {
-                const int e = u * kTapDirs + d;
-                nb[d] = tin + KG * ((nw[e / 2] >> (16 * (e % 2))) & 0xffffu);
-            }
-            const uint32_t tW4 = nb[0][4], tE0 = nb[1][0], tE2 = nb[1][2], tN8 = nb[2][8];
-            const uint32_t tNE8 = nb[3][8], tS0 = nb[4][0], tS1 = nb[4][1], tSW4 = nb[5][4];
+            // the 8 taps, from the 6 neighbour groups (uint16 indices W E N NE S SW)
+            const uint32_t e0 = tq[3 * u], e1 = tq[3 * u + 1], e2 = tq[3 * u + 2];
+            const uint8_t *nbW = tin + KG * (e0 & 0xffffu), *nbE = tin + KG * (e0 >> 16);
+            const uint8_t *nbN = tin + KG * (e1 & 0xffffu), *nbNE = tin + KG * (e1 >> 16);
+            const uint8_t *nbS = tin + KG * (e2 & 0xffffu), *nbSW = tin + KG * (e2 >> 16);
+            const uint32_t tW4 = nbW[4], tE0 = nbE[0], tE2 = nbE[2], tN8 = nbN[8];
+            const uint32_t tNE8 = nbNE[8], tS0 = nbS[0], tS1 = nbS[1], tSW4 = nbSW[4];
             // window rows: bytes 0..3 in lo, 4..5 in hi (columns x = -1..4)
-            uint32_t lo[6], hi[6];
-            lo[0] = tN8 << 8;
-            hi[0] = tNE8 << 8;
-            lo[1] = (rw0 << 8) | tW4;
-            hi[1] = (rw0 >> 24) | (tE0 << 8);
-            lo[2] = rw1 << 8;
-            hi[2] = (rw1 >> 24) | (tE2 << 8);
-            lo[3] = rw2 << 8;
-            hi[3] = rw2 >> 24;
-            lo[4] = rw3 << 8;
-            hi[4] = 0;
-            lo[5] = tSW4 | (tS0 << 8) | (tS1 << 16);
-            hi[5] = 0;
-            const uint32_t pl01 = lo[0] + lo[1], pl23 = lo[2] + lo[3], pl45 = lo[4] + lo[5];
-            const uint32_t ph01 = hi[0] + hi[1], ph23 = hi[2] + hi[3], ph45 = hi[4] + hi[5];
-            const uint32_t vl[4] = {pl01 + lo[2], lo[1] + pl23, pl23 + lo[4], lo[3] + pl45};
-            const uint32_t vh[4] = {ph01 + hi[2], hi[1] + ph23, ph23 + hi[4], hi[3] + ph45};
+            const uint32_t lo0 = tN8 << 8, hi0 = tNE8 << 8;
+            const uint32_t lo1 = (rw0 << 8) | tW4, hi1 = (rw0 >> 24) | (tE0 << 8);
+            const uint32_t lo2 = rw1 << 8, hi2 = (rw1 >> 24) | (tE2 << 8);
+            const uint32_t lo3 = rw2 << 8, hi3 = rw2 >> 24;
+            const uint32_t lo4 = rw3 << 8;
+            const uint32_t lo5 = tSW4 | (tS0 << 8) | (tS1 << 16);
+            const uint32_t pl23 = lo2 + lo3;
+            const uint32_t vl[4] = {lo0 + lo1 + lo2, lo1 + pl23, pl23 + lo4, lo3 + lo4 + lo5};
+            const uint32_t ph12 = hi1 + hi2;
+            const uint32_t vh[4] = {hi0 + ph12, ph12 + hi3, hi2 + hi3, hi3};
             uint32_t S[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 S[j] = vl[j] + __funnelshift_r(vl[j], vh[j], 8) + __funnelshift_r(vl[j], vh[j], 16);
             // sums in lid order: block positions 0 1 4 2 | 3 6 8 9 | 12
-            const uint32_t tg0 = prmt(S[0], S[1], 0x2410u);
-            const uint32_t tg1 = prmt(prmt(S[0], S[1], 0x8863u), S[2], 0x5410u);
-            const uint32_t tg2 = S[3] & 0xffu;
-            const uint32_t tg[3] = {tg0, tg1, tg2};
+            const uint32_t tg[3] = {prmt(S[0], S[1], 0x2410u),
+                                    prmt(prmt(S[0], S[1], 0x8863u), S[2], 0x5410u), S[3] & 0xffu};
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 const int b = b0 + 4 * m;
-                if (b / 4 <= KG) {
+                if (b / 4 <= NW) {
                     T[b / 4] |= tg[m] << ((b % 4) * 8);
-                    if ((b % 4) && b / 4 + 1 <= KG) T[b / 4 + 1] |= tg[m] >> (32 - (b % 4) * 8);
+                    if ((b % 4) && b / 4 + 1 <= NW) T[b / 4 + 1] |= tg[m] >> (32 - (b % 4) * 8);
                 }
             }
         }
-        uint32_t o[KG];
-#pragma unroll
-        for (int i = 0; i < KG; ++i) o[i] = rule4(io.rule.lut, T[i], v[i]);
-        // output bytes [36q, 36q + 36) of the tile; words straddling the
+        // output bytes [9Uq, 9U(q+1)) of the tile; words straddling the
         // neighbouring units' bytes are written byte by byte
-        uint8_t *ob = io.ostage + io.a_out + 36 * q;
-        const int m = (io.a_out + 36 * q) & 3;
+        uint8_t *ob = io.ostage + io.a_out + 9 * U * q;
+        const int m = (io.a_out + 9 * U * q) & 3;
+        uint32_t o[NW];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) o[i] = rule4(io.rule.lut, T[i], v[i]);
         if (m == 0) {
 #pragma unroll
-            for (int i = 0; i < KG; ++i) sts32(ob + 4 * i, o[i]);
+            for (int i = 0; i < NW; ++i) sts32(ob + 4 * i, o[i]);
         } else {
             uint8_t *al = ob - m + 4;            // first whole word
             const uint32_t sl = 8u * (uint32_t)(4 - m);
 #pragma unroll
-            for (int i = 0; i < KG - 1; ++i) sts32(al + 4 * i, __funnelshift_r(o[i], o[i + 1], sl));
+            for (int i = 0; i < NW - 1; ++i) sts32(al + 4 * i, __funnelshift_r(o[i], o[i + 1], sl));
             for (int j = 0; j < 4 - m; ++j) ob[j] = (uint8_t)(o[0] >> (8 * j));
-            for (int j = 0; j < m; ++j) ob[36 - m + j] = (uint8_t)(o[KG - 1] >> (8 * (4 - m + j)));
+            for (int j = 0; j < m; ++j) ob[9 * U - m + j] = (uint8_t)(o[NW - 1] >> (8 * (4 - m + j)));
         }
     }
 };
@@ -1055,7 +1046,7 @@ struct PolicyOf<2, kModeGroup4> { using type = GroupPolicy<4>; };
 template <>
 struct PolicyOf<2, kModeQuad> { using type = QuadPolicy; };
 template <>
-struct PolicyOf<2, kModeTap> { using type = TapPolicy; };
+struct PolicyOf<2, kModeTap> { using type = TapPolicy<kTapUnit>; };
 
 // A tile of the launch resolved to its instance's buffers, table and rule.
 struct TileRef {
