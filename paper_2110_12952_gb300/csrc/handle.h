@@ -46,6 +46,7 @@ struct StepPlan {
     int16_t rel_of_lid[16] = {}; // cell of the group -> offset from the window base
     int xoff = 0;                // box byte of padded column 0 (3 in quad mode)
     int tapz = 0;                // tap mode: index of the all-zero group
+    int nq = 0;                  // tap mode: units per tile
     uint32_t row_sel[8] = {};    // quad mode: byte selectors, group cells -> block rows
     uint32_t pack_sel[9] = {};   // quad mode: byte selectors, block sums -> cell order
 };

@@ -46,6 +46,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "handle.h"
@@ -66,6 +67,7 @@ struct StepArgs {
     int ntab;              // entries of the shared table (cells or groups)
     int KG;                // cells per group (group / quad mode)
     int tapz;              // tap mode: index of the all-zero group
+    int nq;                // tap mode: units per tile
     const uint32_t *tab;   // cell mode: box offset per cell; else window base per group
     const uint32_t *ring;
     const int32_t *nbr;
@@ -140,20 +142,64 @@ static int group_levels(const fractal *f)
 enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10 };
 
 // ---- tap mode: the Sierpinski triangle with offsets (0,0), (1,0), (0,1)
-// A level-2 group is 9 cells (lid 0..8 at (0,0) (1,0) (0,1) (2,0) (3,0)
-// (2,1) (0,2) (1,2) (0,3)) filling a 4x4 block.  The 6x6 window of a block
-// needs, besides its own cells, only 8 border cells ("taps") that are
-// members of a neighbouring block and touch a member of the block.  They
-// come from 6 neighbouring groups, in the order W, E, N, NE, S, SW.
+// A level-2 group is 9 cells (lid 0..8 at kPosX/kPosY) filling a 4x4 block.
+// The 6x6 window of a block needs, besides its own cells, only 8 border
+// cells ("taps") that are members of a neighbouring block and touch a
+// member of the block.  They come from 6 neighbouring groups, in the order
+// W, E, N, NE, S, SW.
 constexpr int kTapDirs = 6;
-constexpr int kTapUnit = 8;    // groups per thread
 constexpr int kTapDx[kTapDirs] = {-1, 1, 0, 1, 0, -1};
 constexpr int kTapDy[kTapDirs] = {0, 0, -1, -1, 1, 1};
 constexpr int kTaps = 8;
-// dir index, lid in that neighbour, window row, window column (0..5)
+// dir index, lid in that neighbour, window row, window column (0..5); in
+// the order W4 E0 E2 N8 NE8 S0 S1 SW4 (direction, then lid)
 constexpr int kTap[kTaps][4] = {{0, 4, 1, 0}, {1, 0, 1, 5}, {1, 2, 2, 5}, {2, 8, 0, 1},
                                 {3, 8, 0, 5}, {4, 0, 5, 1}, {4, 1, 5, 2}, {5, 4, 5, 0}};
 static const int32_t kTriangleOffsets[6] = {0, 0, 1, 0, 0, 1};
+
+// A thread owns a unit: 9 consecutive groups (81 cells, a level-4 subtree),
+// whose groups sit in the 4x4 block of groups at the same positions as the
+// cells of a group in its block (two base-3 digits each picking offset
+// (0,0), (1,0) or (0,1) at its scale).
+constexpr int kUnitGroups = 9;
+constexpr int kUnitCells = 81;
+constexpr int kPosX[9] = {0, 1, 0, 2, 3, 2, 0, 1, 0};
+constexpr int kPosY[9] = {0, 0, 1, 0, 0, 1, 2, 2, 3};
+// The 12 groups around a unit that its taps read (position relative to the
+// unit's first group, in groups) and the 14 tap cells in them.
+constexpr int kExtGroups = 12;
+constexpr int kExtDx[kExtGroups] = {0, 1, 2, 3, 4, 4, -1, -1, -1, -1, -1, 0};
+constexpr int kExtDy[kExtGroups] = {-1, -1, -1, -1, -1, 0, 0, 1, 2, 3, 4, 4};
+constexpr int kExtCells = 14;
+constexpr int kXg[kExtCells] = {0, 1, 2, 3, 4, 5, 5, 6, 7, 8, 9, 10, 11, 11};
+constexpr int kXlid[kExtCells] = {8, 8, 8, 8, 8, 0, 2, 4, 4, 4, 4, 4, 0, 1};
+constexpr int kSrcZero = -1, kSrcBad = -2, kSrcExt = 1000;
+
+// Source of tap t of group j of a unit: byte 9 j' + lid of the unit (a
+// group of the same unit), kSrcZero (a hole of the unit's block) or
+// kSrcExt + c (external tap cell c).
+constexpr int tap_src(int j, int t)
+{
+    const int nx = kPosX[j] + kTapDx[kTap[t][0]], ny = kPosY[j] + kTapDy[kTap[t][0]];
+    const int lid = kTap[t][1];
+    if (nx >= 0 && nx < 4 && ny >= 0 && ny < 4) {
+        for (int g = 0; g < kUnitGroups; ++g)
+            if (kPosX[g] == nx && kPosY[g] == ny) return 9 * g + lid;
+        return kSrcZero;
+    }
+    for (int c = 0; c < kExtCells; ++c)
+        if (kExtDx[kXg[c]] == nx && kExtDy[kXg[c]] == ny && kXlid[c] == lid) return kSrcExt + c;
+    return kSrcBad;
+}
+
+constexpr bool unit_taps_resolved()
+{
+    for (int j = 0; j < kUnitGroups; ++j)
+        for (int t = 0; t < kTaps; ++t)
+            if (tap_src(j, t) == kSrcBad) return false;
+    return true;
+}
+static_assert(unit_taps_resolved(), "every tap outside a unit's block is one of its external cells");
 
 static bool is_triangle(const fractal *f)
 {
@@ -163,14 +209,15 @@ static bool is_triangle(const fractal *f)
     return true;
 }
 
-// Tables of tap mode for tile depth L: per unit of 4 groups, the 6 neighbour
-// group indices of each group (uint16; halo groups continue after the
-// tile's NG groups, index NG + H is an all-zero group), and the halo bytes to
-// fetch per tile (ring entries: byte offset from the tile's first cell in the
-// stage | tile-table slot << 24, cell offset in the neighbouring tile).
+// Tables of tap mode for tile depth L (4 <= L): per unit, the byte offsets
+// 9 g (uint16, two per word) of its 12 external groups from the tile's
+// first cell in the stage, where halo groups continue after the tile's NG
+// groups and group NG + H is all zero; and the halo bytes to fetch per tile
+// (ring entries: byte offset from the tile's first cell in the stage |
+// tile-table slot << 24, cell offset in the neighbouring tile).
 struct TapTables {
     int NG = 0, NQ = 0, H = 0;
-    std::vector<uint32_t> words;   // NQ * 12
+    std::vector<uint32_t> words;   // NQ * 6
     std::vector<uint32_t> ring;
     bool ok = false;
 };
@@ -181,12 +228,12 @@ static int64_t host_nu(const fractal *f, const int q[3], int L);
 static TapTables tap_tables(const fractal *f, int L)
 {
     TapTables t;
-    if (!is_triangle(f) || L < 2) return t;
+    if (!is_triangle(f) || L < 4) return t;
     const int NB = 1 << (L - 2);            // blocks per side
     int NG = 1;
     for (int i = 0; i < L - 2; ++i) NG *= 3;
     t.NG = NG;
-    t.NQ = (NG + kTapUnit - 1) / kTapUnit;
+    t.NQ = NG / kUnitGroups;
     std::vector<int> M((size_t)NB * NB, -1);
     std::vector<int> bx(NG), by(NG);
     for (int g = 0; g < NG; ++g) {
@@ -195,6 +242,16 @@ static TapTables tap_tables(const fractal *f, int L)
         bx[g] = c[0];
         by[g] = c[1];
         M[(size_t)c[1] * NB + c[0]] = g;
+    }
+    // the cell layout of a group and the group layout of a unit
+    for (int lid = 0; lid < 9; ++lid) {
+        int c[3];
+        host_lambda(f, lid, 2, c);
+        if (c[0] != kPosX[lid] || c[1] != kPosY[lid]) return t;
+    }
+    for (int g = 0; g < NG; ++g) {
+        const int g0 = g - g % kUnitGroups;
+        if (bx[g] != bx[g0] + kPosX[g % kUnitGroups] || by[g] != by[g0] + kPosY[g % kUnitGroups]) return t;
     }
     // check the constant tap list against the fractal: every border cell of
     // a window that is a member and touches a member of the block is a tap
@@ -229,13 +286,16 @@ static TapTables tap_tables(const fractal *f, int L)
             }
         if (found != kTaps) return t;
     }
-    // neighbour groups; halo slots for groups of neighbouring tiles
+    uint32_t ext_lids[kExtGroups] = {};
+    for (int c = 0; c < kExtCells; ++c) ext_lids[kXg[c]] |= 1u << kXlid[c];
+    // external groups of every unit; halo slots for groups of neighbouring tiles
     std::map<std::pair<int, int>, int> slot_of;   // (tile-table slot, group there) -> halo slot
     std::vector<std::pair<int, int>> slots;
-    std::vector<int> nbr((size_t)t.NQ * kTapUnit * kTapDirs, -2);
-    for (int g = 0; g < NG; ++g)
-        for (int d = 0; d < kTapDirs; ++d) {
-            int nx = bx[g] + kTapDx[d], ny = by[g] + kTapDy[d];
+    std::vector<uint32_t> lids_read;               // per halo slot: mask of the lids some tap reads
+    std::vector<int> ext((size_t)t.NQ * kExtGroups);
+    for (int q = 0; q < t.NQ; ++q)
+        for (int e = 0; e < kExtGroups; ++e) {
+            int nx = bx[kUnitGroups * q] + kExtDx[e], ny = by[kUnitGroups * q] + kExtDy[e];
             const int tdx = nx < 0 ? -1 : (nx >= NB ? 1 : 0), tdy = ny < 0 ? -1 : (ny >= NB ? 1 : 0);
             nx = (nx + NB) % NB;
             ny = (ny + NB) % NB;
@@ -251,25 +311,29 @@ static TapTables tap_tables(const fractal *f, int L)
                     if (it == slot_of.end()) {
                         it = slot_of.emplace(key, (int)slots.size()).first;
                         slots.push_back(key);
+                        lids_read.push_back(0);
                     }
+                    lids_read[it->second] |= ext_lids[e];
                     v = -100 - it->second;            // halo slot, resolved below
                 }
             }
-            nbr[(size_t)g * kTapDirs + d] = v;
+            ext[(size_t)q * kExtGroups + e] = v;
         }
     t.H = (int)slots.size();
     const int zero = NG + t.H;
-    if (zero >= 65536) return t;
-    // 3 words per group (6 uint16: W E | N NE | S SW), groups in order
-    t.words.assign((size_t)t.NQ * kTapUnit * 3, 0);
-    for (int g = 0; g < t.NQ * kTapUnit; ++g)
-        for (int d = 0; d < kTapDirs; ++d) {
-            int v = g < NG ? nbr[(size_t)g * kTapDirs + d] : -2;
-            const uint32_t idx = (v == -2) ? (uint32_t)zero : (v <= -100 ? (uint32_t)(NG + (-100 - v)) : (uint32_t)v);
-            t.words[(size_t)g * 3 + d / 2] |= idx << (16 * (d % 2));
+    if (9 * zero + 8 >= 65536) return t;
+    t.words.assign((size_t)t.NQ * kExtGroups / 2, 0);
+    for (int q = 0; q < t.NQ; ++q)
+        for (int e = 0; e < kExtGroups; ++e) {
+            const int v = ext[(size_t)q * kExtGroups + e];
+            const uint32_t g = (v == -2) ? (uint32_t)zero : (v <= -100 ? (uint32_t)(NG + (-100 - v)) : (uint32_t)v);
+            t.words[(size_t)q * (kExtGroups / 2) + e / 2] |= (9u * g) << (16 * (e % 2));
         }
+    // only the halo cells that a tap reads are staged; the other bytes of a
+    // halo group are never read
     for (int hs = 0; hs < t.H; ++hs)
         for (int lid = 0; lid < 9; ++lid) {
+            if (!((lids_read[hs] >> lid) & 1u)) continue;
             t.ring.push_back((uint32_t)(9 * (NG + hs) + lid) | ((uint32_t)slots[hs].first << 24));
             t.ring.push_back((uint32_t)(9 * slots[hs].second + lid));
         }
@@ -299,12 +363,12 @@ static Geometry plan_geometry(const fractal *f, int L)
     g.block = 256;
     const bool grp = g.G > 0 && L >= g.G && ipow(f->k, g.G) <= kMaxGroup;
     g.halo = 0;
-    if (grp && is_triangle(f) && L >= 2 && (ipow(f->k, L - 2) + kTapUnit - 1) / kTapUnit <= 256) {
+    if (grp && is_triangle(f) && L >= 4 && ipow(f->k, L - 4) <= 256) {
         const TapTables t = tap_tables(f, L);
         if (t.ok) {
             g.mode = kModeTap;
             g.Px = g.Py = g.planes = 0;
-            g.tab_entries = (int64_t)t.NQ * kTapUnit * 3;
+            g.tab_entries = 0;   // the unit tables live in registers
             g.halo = t.H;
             g.block = std::max<int64_t>(64, ((int64_t)t.NQ + 31) / 32 * 32);
             g.box_bytes = 0;
@@ -353,9 +417,9 @@ static Layout plan_layout(const fractal *f, int L)
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
     y.nstage = (g.mode == kModeQuad) ? 2 : (g.mode == kModeTap ? 3 : nstages());
-    // slack: 16-byte rounding of the bulk copy, halo and zero groups, and
-    // the tap units' whole-word reads and writes past the tile's last cell
-    y.tile_bytes = round16(KL + 64 + 9 * (g.halo + 1) + 9 * kTapUnit);
+    // slack: 16-byte rounding of the bulk copy, whole-word reads and writes
+    // past the tile's last cell; tap mode: halo and zero groups
+    y.tile_bytes = round16(KL + 64 + (g.mode == kModeTap ? 9 * (g.halo + 1) : 0));
     y.stage_bytes = 4 * nbr_width(f->dim) + kStagePad + y.tile_bytes;
     int64_t off = y.nstage * y.stage_bytes;
     y.off_bar = off;
@@ -367,7 +431,7 @@ static Layout plan_layout(const fractal *f, int L)
     y.off_tab = off;
     off += round16(4 * g.tab_entries);
     y.off_out = off;
-    off += kStagePad + y.tile_bytes;
+    off += (g.mode == kModeTap ? 2 : 1) * (kStagePad + y.tile_bytes);   // tap: double-buffered
     y.total = off;
     return y;
 }
@@ -504,6 +568,7 @@ int ensure_step_plan(fractal *f)
         const TapTables t = tap_tables(f, L);
         p.KG = 9;
         p.tapz = t.NG + t.H;
+        p.nq = t.NQ;
         tab = t.words;
         ring = t.ring;
     } else {
@@ -681,10 +746,11 @@ __device__ __forceinline__ uint32_t rule4(const uint32_t lut[4], uint32_t t, uin
 {
     const uint32_t x = t | (t >> 4);
     const uint32_t sel = prmt(x, 0u, 0x3120u);   // nibble i = total of cell i
-    const uint32_t rd = prmt(lut[0], lut[1], sel) & 0x01010101u;
-    const uint32_t rl = prmt(lut[2], lut[3], sel) & 0x01010101u;
-    const uint32_t m = alive * 0xffu;
-    return (rl & m) | (rd & ~m);
+    const uint32_t rd = prmt(lut[0], lut[1], sel);
+    const uint32_t rl = prmt(lut[2], lut[3], sel);
+    // bit 0 of each byte: the live table's where the cell is alive (alive
+    // bytes are 0 or 1), the dead table's elsewhere
+    return ((rl & alive) | (rd & ~alive)) & 0x01010101u;
 }
 
 // Window of the block of one group: rows r = 0..SG+1, bytes 0..SG+1 of the
@@ -919,36 +985,141 @@ struct QuadPolicy {
     }
 };
 
-// ---- tap policy (the triangle; see kTap): no box.  A thread owns U
-// consecutive groups (9U cells); it reads its cells and the 8 taps of each
-// group straight from the stage, where the halo groups follow the tile's own
-// groups, and writes 9U/4 output words.
-template <int U>
+// ---- tap policy (the triangle; see kTap and kPosX): no box.  A thread
+// owns one unit (9 groups, 81 cells).  Of the 8 taps of each group, those in
+// a group of the same unit come from the thread's registers, those in a hole
+// of the unit's block are 0, and the 14 external ones are read from the
+// stage through the unit's 12 external group offsets, which are the same
+// for every tile and stay in registers.  The totals of a group are summed
+// in cell order: each of its three level-1 triangles (lids 0-2, 3-5, 6-8)
+// gives its sum to its own three cells; the five edges between them (lids
+// 1-3, 1-5, 2-6, 2-7, 5-7) and the taps add the rest.
+
+// tap byte, 0 or 1, from its source (see tap_src)
+template <int S>
+__device__ __forceinline__ uint32_t tap_byte(const uint32_t *v, const uint32_t *x)
+{
+    if constexpr (S == kSrcZero) return 0u;
+    else if constexpr (S >= kSrcExt) return x[S - kSrcExt];
+    else return prmt(v[S >> 2], 0u, 0x4440u | (uint32_t)(S & 3));
+}
+
+// bytes P .. P+3 of a byte stream held in words
+template <int P>
+__device__ __forceinline__ uint32_t win(const uint32_t *v)
+{
+    if constexpr (P % 4 == 0) return v[P / 4];
+    else return __funnelshift_r(v[P / 4], v[P / 4 + 1], 8 * (P % 4));
+}
+
+// add the 4 bytes w at byte P of a stream whose bytes there are still 0
+template <int P>
+__device__ __forceinline__ void put(uint32_t *S, uint32_t w)
+{
+    if constexpr (P % 4 == 0) S[P / 4] += w;
+    else {
+        S[P / 4] += w << (8 * (P % 4));
+        S[P / 4 + 1] += w >> (32 - 8 * (P % 4));
+    }
+}
+
+// totals (3x3 sums including the cell) of group J of a unit, added to the
+// unit's stream S at bytes 9J .. 9J+8
+template <int J>
+__device__ __forceinline__ void unit_group(const uint32_t *v, const uint32_t *x, uint32_t *S)
+{
+    constexpr int b = 9 * J;
+    const uint32_t A = win<b>(v), B = win<b + 4>(v);     // lids 0-3, 4-7
+    const uint32_t P0 = A * 0x010101u;                   // byte 2: l0 + l1 + l2
+    const uint32_t P1 = win<b + 3>(v) * 0x010101u;      // byte 2: l3 + l4 + l5
+    const uint32_t P2 = win<b + 6>(v) * 0x010101u;      // byte 2: l6 + l7 + l8
+    const uint32_t w4 = tap_byte<tap_src(J, 0)>(v, x), e0 = tap_byte<tap_src(J, 1)>(v, x);
+    const uint32_t e2 = tap_byte<tap_src(J, 2)>(v, x), n8 = tap_byte<tap_src(J, 3)>(v, x);
+    const uint32_t ne8 = tap_byte<tap_src(J, 4)>(v, x), s0 = tap_byte<tap_src(J, 5)>(v, x);
+    const uint32_t s1 = tap_byte<tap_src(J, 6)>(v, x), sw4 = tap_byte<tap_src(J, 7)>(v, x);
+    // lids 0..3: t0 + N8 + W4 | t0 + l3 + l5 + N8 | t0 + l6 + l7 + W4 | t1 + l1
+    const uint32_t T0 = prmt(P0, P1, 0x6222u) + (prmt(A, B, 0x1630u) & 0xffffff00u) + prmt(B, 0u, 0x4314u) +
+                        w4 * 0x00010001u + n8 * 0x00000101u;
+    // lids 4..7: t1 + NE8 + E0 + E2 | t1 + l1 + l7 | t2 + l2 | t2 + l2 + l5
+    const uint32_t T1 = prmt(P1, P2, 0x6622u) + prmt(A, 0u, 0x2214u) + prmt(B, 0u, 0x1434u) + (ne8 + e0 + e2);
+    // lid 8 (byte 2): t2 + SW4 + S0 + S1
+    const uint32_t T2 = P2 + ((sw4 + s0 + s1) << 16);
+    put<b>(S, T0);
+    put<b + 4>(S, T1);
+    S[(b + 8) / 4] += prmt(T2, 0u, (0x4444u & ~(0xfu << (4 * ((b + 8) % 4)))) | (2u << (4 * ((b + 8) % 4))));
+}
+
+// store bytes 0..80 of the stream o at ob, where ob - M is word aligned
+// (whole words where they hold only this unit's bytes, bytes elsewhere)
+template <int M>
+__device__ __forceinline__ void store_unit(uint8_t *ob, const uint32_t *o)
+{
+    constexpr int H = (4 - M) & 3;                  // bytes before the first whole word
+    constexpr int NWF = (kUnitCells - H) / 4;       // whole words
+    constexpr int TL = kUnitCells - H - 4 * NWF;    // bytes after them
+#pragma unroll
+    for (int j = 0; j < H; ++j) ob[j] = (uint8_t)(o[0] >> (8 * j));
+#pragma unroll
+    for (int i = 0; i < NWF; ++i) {
+        const int P = H + 4 * i;
+        const uint32_t w = (P % 4 == 0) ? o[P / 4] : __funnelshift_r(o[P / 4], o[P / 4 + 1], 8 * (P % 4));
+        sts32(ob + P, w);
+    }
+#pragma unroll
+    for (int j = 0; j < TL; ++j) {
+        const int P = H + 4 * NWF + j;
+        ob[P] = (uint8_t)(o[P / 4] >> (8 * (P % 4)));
+    }
+}
+
+// external tap cell C, 0 or 1, read from the stage
+template <int C>
+__device__ __forceinline__ uint32_t ext_tap(const uint8_t *tin, const uint32_t *e)
+{
+    constexpr int g = kXg[C], lid = kXlid[C];
+    const uint32_t o = (g & 1) ? (e[g / 2] >> 16) : (e[g / 2] & 0xffffu);
+    return min((uint32_t)tin[o + lid], 1u);
+}
+
+template <int... C>
+__device__ __forceinline__ void ext_taps(const uint8_t *tin, const uint32_t *e, uint32_t *x,
+                                         std::integer_sequence<int, C...>)
+{
+    ((x[C] = ext_tap<C>(tin, e)), ...);
+}
+
 struct TapPolicy {
     static constexpr bool kRingInTile = true;   // halo bytes go after the tile's bytes
-    static constexpr int KG = 9;
-    static constexpr int NW = KG * U / 4;       // words per unit
-    struct Regs {};
-    __device__ static void init(const StepArgs &, Regs &) {}
-
-    __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *, const uint32_t *, Regs &)
-    {
-        // the all-zero group (after the halo groups; the bulk copy may have
-        // written there)
-        if (threadIdx.x < KG) const_cast<uint8_t *>(io.data)[io.a_in + KG * a.tapz + threadIdx.x] = 0;
-    }
-
-    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *, const uint32_t *tab,
-                                   Regs &)
+    static constexpr int NW = (kUnitCells + 3) / 4;   // 21 words per unit
+    struct Regs {
+        uint32_t e[kExtGroups / 2];   // byte offsets 9 g of the external groups, two per word
+    };
+    __device__ static void init(const StepArgs &a, Regs &R)
     {
         const int q = threadIdx.x;
-        const int nq = a.ntab / (3 * U);
-        if (q >= nq) return;
+#pragma unroll
+        for (int k = 0; k < kExtGroups / 2; ++k)
+            R.e[k] = (q < a.nq) ? __ldg(a.tab + (kExtGroups / 2) * q + k) : 0u;
+    }
+    // the all-zero group, after the halo groups (the bulk copy may have
+    // written there); `tin` is the tile's first cell in the stage
+    __device__ static void fill(const StepArgs &a, uint8_t *tin)
+    {
+        if (threadIdx.x < 9) tin[9 * a.tapz + threadIdx.x] = 0;
+    }
+    __device__ static void scatter(const StepArgs &, const TileIO &, uint8_t *, const uint32_t *, Regs &) {}
+
+    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *, const uint32_t *,
+                                   Regs &R)
+    {
+        const int q = threadIdx.x;
+        if (q >= a.nq) return;
         const uint8_t *tin = io.data + io.a_in;
-        const int off = io.a_in + 9 * U * q;
+        const int off = io.a_in + kUnitCells * q;
         const uint8_t *wp = io.data + (off & ~3);
         const uint32_t sh = (uint32_t)(off & 3) * 8u;
-        uint32_t v[NW + 1];
+        // the unit's 81 cells (bytes 81..83 of v belong to whoever follows)
+        uint32_t v[NW];
         {
             uint32_t w[NW + 1];
 #pragma unroll
@@ -957,80 +1128,35 @@ struct TapPolicy {
 #pragma unroll
             for (int i = 0; i < NW; ++i) {
                 v[i] = __funnelshift_r(w[i], w[i + 1], sh);
-                any |= v[i];
+                any |= (i == NW - 1) ? (v[i] & 0xffu) : v[i];
             }
-            v[NW] = 0;
             if (any & 0xfefefefeu) {
 #pragma unroll
                 for (int i = 0; i < NW; ++i) v[i] = bytes_to_01(v[i]);
             }
         }
-        uint32_t T[NW + 1];
+        uint32_t x[kExtCells];
+        ext_taps(tin, R.e, x, std::make_integer_sequence<int, kExtCells>());
+        uint32_t S[NW];
 #pragma unroll
-        for (int i = 0; i <= NW; ++i) T[i] = 0;
-        const uint32_t *tq = tab + 3 * U * q;
+        for (int i = 0; i < NW; ++i) S[i] = 0;
+        unit_group<0>(v, x, S);
+        unit_group<1>(v, x, S);
+        unit_group<2>(v, x, S);
+        unit_group<3>(v, x, S);
+        unit_group<4>(v, x, S);
+        unit_group<5>(v, x, S);
+        unit_group<6>(v, x, S);
+        unit_group<7>(v, x, S);
+        unit_group<8>(v, x, S);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int b0 = KG * u;
-            const uint32_t g0w = __funnelshift_r(v[b0 / 4], v[b0 / 4 + 1], (b0 % 4) * 8);
-            const uint32_t g1w = __funnelshift_r(v[b0 / 4 + 1], v[b0 / 4 + 2], (b0 % 4) * 8);
-            const uint32_t g2w = __funnelshift_r(v[b0 / 4 + 2], v[b0 / 4 + 3 <= NW ? b0 / 4 + 3 : NW], (b0 % 4) * 8);
-            // block rows (cells x = 0..3): lids 0 1 3 4 / 2 - 5 - / 6 7 - - / 8 - - -
-            const uint32_t rw0 = prmt(g0w, g1w, 0x4310u);
-            const uint32_t rw1 = prmt(g0w, g1w, 0x8582u);
-            const uint32_t rw2 = prmt(g1w, 0u, 0x8832u);
-            const uint32_t rw3 = g2w & 0xffu;
-            // the 8 taps, from the 6 neighbour groups (uint16 indices W E N NE S SW)
-            const uint32_t e0 = tq[3 * u], e1 = tq[3 * u + 1], e2 = tq[3 * u + 2];
-            const uint8_t *nbW = tin + KG * (e0 & 0xffffu), *nbE = tin + KG * (e0 >> 16);
-            const uint8_t *nbN = tin + KG * (e1 & 0xffffu), *nbNE = tin + KG * (e1 >> 16);
-            const uint8_t *nbS = tin + KG * (e2 & 0xffffu), *nbSW = tin + KG * (e2 >> 16);
-            const uint32_t tW4 = nbW[4], tE0 = nbE[0], tE2 = nbE[2], tN8 = nbN[8];
-            const uint32_t tNE8 = nbNE[8], tS0 = nbS[0], tS1 = nbS[1], tSW4 = nbSW[4];
-            // window rows: bytes 0..3 in lo, 4..5 in hi (columns x = -1..4)
-            const uint32_t lo0 = tN8 << 8, hi0 = tNE8 << 8;
-            const uint32_t lo1 = (rw0 << 8) | tW4, hi1 = (rw0 >> 24) | (tE0 << 8);
-            const uint32_t lo2 = rw1 << 8, hi2 = (rw1 >> 24) | (tE2 << 8);
-            const uint32_t lo3 = rw2 << 8, hi3 = rw2 >> 24;
-            const uint32_t lo4 = rw3 << 8;
-            const uint32_t lo5 = tSW4 | (tS0 << 8) | (tS1 << 16);
-            const uint32_t pl23 = lo2 + lo3;
-            const uint32_t vl[4] = {lo0 + lo1 + lo2, lo1 + pl23, pl23 + lo4, lo3 + lo4 + lo5};
-            const uint32_t ph12 = hi1 + hi2;
-            const uint32_t vh[4] = {hi0 + ph12, ph12 + hi3, hi2 + hi3, hi3};
-            uint32_t S[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                S[j] = vl[j] + __funnelshift_r(vl[j], vh[j], 8) + __funnelshift_r(vl[j], vh[j], 16);
-            // sums in lid order: block positions 0 1 4 2 | 3 6 8 9 | 12
-            const uint32_t tg[3] = {prmt(S[0], S[1], 0x2410u),
-                                    prmt(prmt(S[0], S[1], 0x8863u), S[2], 0x5410u), S[3] & 0xffu};
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const int b = b0 + 4 * m;
-                if (b / 4 <= NW) {
-                    T[b / 4] |= tg[m] << ((b % 4) * 8);
-                    if ((b % 4) && b / 4 + 1 <= NW) T[b / 4 + 1] |= tg[m] >> (32 - (b % 4) * 8);
-                }
-            }
-        }
-        // output bytes [9Uq, 9U(q+1)) of the tile; words straddling the
-        // neighbouring units' bytes are written byte by byte
-        uint8_t *ob = io.ostage + io.a_out + 9 * U * q;
-        const int m = (io.a_out + 9 * U * q) & 3;
-        uint32_t o[NW];
-#pragma unroll
-        for (int i = 0; i < NW; ++i) o[i] = rule4(io.rule.lut, T[i], v[i]);
-        if (m == 0) {
-#pragma unroll
-            for (int i = 0; i < NW; ++i) sts32(ob + 4 * i, o[i]);
-        } else {
-            uint8_t *al = ob - m + 4;            // first whole word
-            const uint32_t sl = 8u * (uint32_t)(4 - m);
-#pragma unroll
-            for (int i = 0; i < NW - 1; ++i) sts32(al + 4 * i, __funnelshift_r(o[i], o[i + 1], sl));
-            for (int j = 0; j < 4 - m; ++j) ob[j] = (uint8_t)(o[0] >> (8 * j));
-            for (int j = 0; j < m; ++j) ob[9 * U - m + j] = (uint8_t)(o[NW - 1] >> (8 * (4 - m + j)));
+        for (int i = 0; i < NW; ++i) S[i] = rule4(io.rule.lut, S[i], v[i]);
+        uint8_t *ob = io.ostage + io.a_out + kUnitCells * q;
+        switch ((io.a_out + kUnitCells * q) & 3) {
+        case 0: store_unit<0>(ob, S); break;
+        case 1: store_unit<1>(ob, S); break;
+        case 2: store_unit<2>(ob, S); break;
+        default: store_unit<3>(ob, S); break;
         }
     }
 };
@@ -1046,7 +1172,7 @@ struct PolicyOf<2, kModeGroup4> { using type = GroupPolicy<4>; };
 template <>
 struct PolicyOf<2, kModeQuad> { using type = QuadPolicy; };
 template <>
-struct PolicyOf<2, kModeTap> { using type = TapPolicy<kTapUnit>; };
+struct PolicyOf<2, kModeTap> { using type = TapPolicy; };
 
 // A tile of the launch resolved to its instance's buffers, table and rule.
 struct TileRef {
@@ -1111,36 +1237,197 @@ __device__ __forceinline__ void issue_tile(const StepArgs &a, const TileRef &t, 
     if (data_bytes) bulk_g2s(stage + row_bytes + kStagePad + (b0 - lo), (const void *)b0, data_bytes, bar);
 }
 
-template <int DIM, int MODE, bool MULTI>
-__global__ void __launch_bounds__(256)
-step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
+// After a failed wait: wait (bounded) for the bulk loads still in flight
+// into this block's stages, those of the block's tiles j0 .. j1 (its
+// iteration numbers), so that no copy lands after the block has exited.
+__device__ __forceinline__ void drain_loads(const StepArgs &a, uint64_t *bars, int64_t j0, int64_t j1)
 {
-    using Pol = typename PolicyOf<DIM, MODE>::type;
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.off_bar);
-    uint8_t *box = smem + a.off_box;
-    uint32_t *tab = reinterpret_cast<uint32_t *>(smem + a.off_tab);
-    uint8_t *ostage = smem + a.off_out + kStagePad;
+    if (threadIdx.x != 0) return;
+    for (int64_t j = j0; j <= j1; ++j) {
+        if (blockIdx.x + j * (int64_t)gridDim.x >= a.NT) break;
+        mbar_wait_bounded(&bars[j % a.nstage], (uint32_t)((j / a.nstage) & 1));
+    }
+}
+
+// Input and output stage geometry of one tile.
+__device__ __forceinline__ TileIO tile_io(const StepArgs &a, const TileRef &t, uint8_t *stage, uint8_t *ostage)
+{
+    const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
+    const uintptr_t ostart = (uintptr_t)(t.out + t.T * a.KL);
+    TileIO io;
+    io.data = stage + 4 * a.nbrw + kStagePad;   // data[j] <-> address (start & ~15) + j
+    io.ostage = ostage;
+    io.a_in = (int)(start & 15);
+    io.a_out = (int)(ostart & 15);
+    return io;
+}
+
+// Complete a landed stage for the compute of a ring-in-tile policy: the
+// tile bytes the bulk copy could not cover (unaligned buffer ends), the
+// policy's own bytes and the halo cells, the first kRingRegs per thread
+// from `rv` when they were prefetched.
+template <bool MULTI, class Pol>
+__device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, uint8_t *stage,
+                                           const uint32_t *rv, bool pref)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
+    TileIO io = tile_io(a, t, stage, nullptr);
+    uint8_t *data = const_cast<uint8_t *>(io.data);
+    const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
+    const uintptr_t end = start + (uintptr_t)a.KL;
+    const uintptr_t lo = start & ~(uintptr_t)15;
+    const uintptr_t in_lo = ((uintptr_t)t.in + 15) & ~(uintptr_t)15;
+    const uintptr_t in_hi = ((uintptr_t)t.in + (uintptr_t)t.cells) & ~(uintptr_t)15;
+    uintptr_t b0 = lo > in_lo ? lo : in_lo;
+    uintptr_t b1 = (end + 15) & ~(uintptr_t)15;
+    if (b1 > in_hi) b1 = in_hi;
+    if (b0 > start || b1 < end) {
+        for (int64_t l = tid; l < a.KL; l += nth) {
+            const uintptr_t ad = start + l;
+            if (ad < b0 || ad >= b1) data[ad - lo] = *(const uint8_t *)ad;
+        }
+    }
+    uint8_t *tin = data + io.a_in;
+    Pol::fill(a, tin);
+#pragma unroll
+    for (int k = 0; k < kRingRegs; ++k) {
+        const int e = tid + k * nth;
+        if (e < a.nring) {
+            const uint32_t w0 = __ldg(a.ring + 2 * e);
+            uint32_t v = rv[k];
+            if (!pref) {
+                const int32_t tn = nrow[w0 >> 24];
+                v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+            }
+            tin[w0 & 0xffffff] = v != 0;
+        }
+    }
+    for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
+        const uint32_t w0 = __ldg(a.ring + 2 * e), lw = __ldg(a.ring + 2 * e + 1);
+        const int32_t tn = nrow[w0 >> 24];
+        uint8_t v = 0;
+        if (tn >= 0) v = t.in[(int64_t)tn * a.KL + lw] != 0;
+        tin[w0 & 0xffffff] = v;
+    }
+}
+
+// Tile loop of the policies that compute from the input stage itself, with
+// one block barrier per tile.  Tile i is computed into output stage i & 1;
+// then each thread waits for tile i+1's stage and fills its share of it, and
+// the barrier that follows both closes tile i and opens tile i+1.  After it,
+// thread 0 refills tile i's input stage and stores its output stage (the
+// store of tile i-2 from the same output stage has finished reading it
+// before the barrier).
+template <bool MULTI, class Pol>
+__device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_t *in, uint8_t *out,
+                                                 uint8_t *smem, uint64_t *bars, const uint32_t *tab,
+                                                 typename Pol::Regs &R)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int64_t G = gridDim.x;
+    const int ostride = kStagePad + a.tile_bytes;
+    uint8_t *ostage0 = smem + a.off_out + kStagePad;
+    int64_t Tg = blockIdx.x;
+    if (Tg >= a.NT) return;
+    uint32_t rv[kRingRegs];
+#pragma unroll
+    for (int k = 0; k < kRingRegs; ++k) rv[k] = 0;
+    TileRef t = resolve<MULTI>(a, in, out, Tg);
+    bool ok = mbar_wait_bounded(&bars[0], 0);
+    if (ok) fill_stage<MULTI, Pol>(a, t, smem, rv, false);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
+        drain_loads(a, bars, 0, a.nstage - 1);
+        return;
+    }
+    for (int64_t i = 0;; ++i) {
+        const int s = (int)(i % a.nstage);
+        uint8_t *stage = smem + s * a.stage_bytes;
+        const int64_t Tn = Tg + G;
+        const bool has_next = Tn < a.NT;
+        const int sn = (int)((i + 1) % a.nstage);
+        const uint32_t pn = (uint32_t)(((i + 1) / a.nstage) & 1);
+        uint8_t *next_stage = smem + sn * a.stage_bytes;
+        TileRef tn = t;
+        if (has_next) tn = resolve<MULTI>(a, in, out, Tn);
+        // the next tile's halo values, when its stage has landed already
+        // (never waited for here): the loads stay in flight during the compute
+        bool pref = false;
+        if (has_next && tid < a.nring && mbar_test(&bars[sn], pn)) {
+            const int32_t *nrow_n = reinterpret_cast<const int32_t *>(next_stage);
+#pragma unroll
+            for (int k = 0; k < kRingRegs; ++k) {
+                const int e = tid + k * nth;
+                if (e < a.nring) {
+                    const uint32_t w0 = __ldg(a.ring + 2 * e);
+                    const int32_t tnb = nrow_n[w0 >> 24];
+                    rv[k] = (tnb >= 0) ? tn.in[(int64_t)tnb * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+                }
+            }
+            pref = true;
+        }
+        uint8_t *ostage = ostage0 + (int)(i & 1) * ostride;
+        TileIO io = tile_io(a, t, stage, ostage);
+        tile_rule<MULTI>(a, Tg, io.rule);
+        Pol::compute(a, io, nullptr, tab, R);
+        ok = true;
+        if (has_next) {
+            ok = mbar_wait_bounded(&bars[sn], pn);
+            if (ok) fill_stage<MULTI, Pol>(a, tn, next_stage, rv, pref);
+        }
+        if (tid == 0) bulk_wait_read_all();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
+            drain_loads(a, bars, i + 1, i + a.nstage - 1);
+            break;
+        }
+        const uintptr_t ostart = (uintptr_t)(t.out + t.T * a.KL);
+        const uintptr_t oend = ostart + (uintptr_t)a.KL;
+        const uintptr_t olo = ostart & ~(uintptr_t)15;
+        const uintptr_t c0 = (ostart + 15) & ~(uintptr_t)15;
+        const uintptr_t c1 = oend & ~(uintptr_t)15;
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            const int64_t Tr = Tg + a.nstage * G;
+            if (Tr < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tr), stage, &bars[s]);
+            if (c1 > c0) {
+                bulk_s2g((void *)c0, ostage + (c0 - olo), (uint32_t)(c1 - c0));
+                bulk_commit();
+            }
+        }
+        const uint8_t *tout = ostage + io.a_out;
+        if (c1 > c0) {
+            const int head = (int)(c0 - ostart), tail = (int)(oend - c1);
+            if (tid < head) *(uint8_t *)(ostart + tid) = tout[tid];
+            else if (tid >= 32 && tid < 32 + tail) {
+                const int j = tid - 32;
+                *(uint8_t *)(c1 + j) = ostage[c1 - olo + j];
+            }
+        } else {
+            for (int64_t l = tid; l < a.KL; l += nth) *(uint8_t *)(ostart + l) = tout[l];
+        }
+        if (!has_next) break;
+        Tg = Tn;
+        t = tn;
+    }
+    if (tid == 0) bulk_wait_all();
+}
+
+// Tile loop of the policies that compute from the box: wait for the tile's
+// stage; scatter its cells and halo into the box (halo values prefetched
+// into registers during the previous tile when its stage had landed);
+// barrier; refill the stage with the tile nstage iterations ahead; compute
+// into the output stage; barrier; bulk-store the output stage.
+template <bool MULTI, class Pol>
+__device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in, uint8_t *out, uint8_t *smem,
+                                            uint64_t *bars, uint8_t *box, const uint32_t *tab,
+                                            typename Pol::Regs &R)
+{
     const int tid = threadIdx.x, nth = blockDim.x;
     const int64_t G = gridDim.x;
     const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
-
-    if (tid == 0) {
-        for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
-        fence_proxy_async_smem();
-        for (int s = 0; s < a.nstage; ++s) {
-            const int64_t Tg = blockIdx.x + s * G;
-            if (Tg < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tg), smem + s * a.stage_bytes, &bars[s]);
-        }
-    }
-    for (int i = tid; i < a.box_bytes / 16; i += nth)
-        reinterpret_cast<uint4 *>(box)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < a.ntab; i += nth) tab[i] = a.tab[i];
-    __syncthreads();
-
-    typename Pol::Regs R;
-    Pol::init(a, R);
-
+    uint8_t *ostage = smem + a.off_out + kStagePad;
     uint32_t rv[kRingRegs];   // prefetched halo values of the current tile
 #pragma unroll
     for (int k = 0; k < kRingRegs; ++k) rv[k] = 0;
@@ -1155,6 +1442,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         const bool ok = mbar_wait_bounded(&bars[s], parity);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
+            drain_loads(a, bars, i, i + a.nstage - 1);
             break;
         }
         const TileRef t = resolve<MULTI>(a, in, out, Tg);
@@ -1273,6 +1561,39 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
     if (tid == 0) bulk_wait_all();
 }
 
+template <int DIM, int MODE, bool MULTI>
+__global__ void __launch_bounds__(256)
+step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
+{
+    using Pol = typename PolicyOf<DIM, MODE>::type;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.off_bar);
+    uint8_t *box = smem + a.off_box;
+    uint32_t *tab = reinterpret_cast<uint32_t *>(smem + a.off_tab);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int64_t G = gridDim.x;
+
+    if (tid == 0) {
+        for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
+        fence_proxy_async_smem();
+        for (int s = 0; s < a.nstage; ++s) {
+            const int64_t Tg = blockIdx.x + s * G;
+            if (Tg < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tg), smem + s * a.stage_bytes, &bars[s]);
+        }
+    }
+    for (int i = tid; i < a.box_bytes / 16; i += nth)
+        reinterpret_cast<uint4 *>(box)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < a.ntab; i += nth) tab[i] = a.tab[i];
+    __syncthreads();
+
+    typename Pol::Regs R;
+    Pol::init(a, R);
+    if constexpr (Pol::kRingInTile)
+        one_barrier_loop<MULTI, Pol>(a, in, out, smem, bars, tab, R);
+    else
+        staged_loop<MULTI, Pol>(a, in, out, smem, bars, box, tab, R);
+}
+
 // Byte tables of the rule for the quad policy (see rule4).
 static void rule_tables(uint32_t birth, uint32_t survive, uint32_t lut[4])
 {
@@ -1321,6 +1642,7 @@ static void fill_args(const fractal *f, StepArgs &a)
     a.ntab = p.ntab;
     a.KG = p.KG;
     a.tapz = p.tapz;
+    a.nq = p.nq;
     a.tab = p.pos;
     a.ring = p.ring;
     a.nbr = p.nbr;

@@ -145,7 +145,7 @@ def test_step_exhaustive_all_tile_depths(P, fam, r, levels):
         assert np.array_equal(out.cpu().numpy(), ref), f"L={L}"
 
 
-@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 7, 8, 9])
 def test_triangle_many_tiles_per_cta(P, L):
     # r = 14 gives thousands of tiles at every depth, so each CTA reuses its
     # pipeline stages many times
@@ -155,6 +155,19 @@ def test_triangle_many_tiles_per_cta(P, L):
     x = torch.from_numpy(init).cuda()
     g.tile_levels = L
     assert np.array_equal(g.step(x, steps=2).cpu().numpy(), o.step(init, steps=2)), f"L={L}"
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 7, 8, 9])
+def test_triangle_nonbinary_input_every_depth(P, L):
+    # any nonzero byte is alive: the first generation must read 0..255 as
+    # 0/1 wherever a cell is read (own cells, taps, halo)
+    fam, r = W.TRIANGLE, 12
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    rng = np.random.default_rng(100 + L)
+    raw = (rng.integers(0, 2, size=g.cells) * rng.integers(1, 256, size=g.cells)).astype(np.uint8)
+    g.tile_levels = L
+    out = g.step(torch.from_numpy(raw).cuda(), steps=1)
+    assert np.array_equal(out.cpu().numpy(), o.step(raw, steps=1)), f"L={L}"
 
 
 def test_autotune_keeps_parity(P):
