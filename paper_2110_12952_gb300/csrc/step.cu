@@ -285,6 +285,18 @@ static TapTables tap_tables(const fractal *f, int L)
                 ++found;
             }
         if (found != kTaps) return t;
+        // rule4_sparse: no member has more than 6 member neighbours (the
+        // block's members and the taps are every member its cells touch)
+        int win[6][6] = {};
+        for (int lid = 0; lid < 9; ++lid) win[kPosY[lid] + 1][kPosX[lid] + 1] = 1;
+        for (int k = 0; k < kTaps; ++k) win[kTap[k][2]][kTap[k][3]] = 1;
+        for (int lid = 0; lid < 9; ++lid) {
+            int n = 0;
+            for (int ey = -1; ey <= 1; ++ey)
+                for (int ex = -1; ex <= 1; ++ex)
+                    if (ex || ey) n += win[kPosY[lid] + 1 + ey][kPosX[lid] + 1 + ex];
+            if (n > 6) return t;
+        }
     }
     uint32_t ext_lids[kExtGroups] = {};
     for (int c = 0; c < kExtCells; ++c) ext_lids[kXg[c]] |= 1u << kXlid[c];
@@ -416,7 +428,7 @@ static Layout plan_layout(const fractal *f, int L)
     Layout y;
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
-    y.nstage = (g.mode == kModeQuad) ? 2 : (g.mode == kModeTap ? 3 : nstages());
+    y.nstage = (g.mode == kModeQuad || g.mode == kModeTap) ? 2 : nstages();
     // slack: 16-byte rounding of the bulk copy, whole-word reads and writes
     // past the tile's last cell; tap mode: halo and zero groups
     y.tile_bytes = round16(KL + 64 + (g.mode == kModeTap ? 9 * (g.halo + 1) : 0));
@@ -431,7 +443,7 @@ static Layout plan_layout(const fractal *f, int L)
     y.off_tab = off;
     off += round16(4 * g.tab_entries);
     y.off_out = off;
-    off += (g.mode == kModeTap ? 2 : 1) * (kStagePad + y.tile_bytes);   // tap: double-buffered
+    off += kStagePad + y.tile_bytes;
     y.total = off;
     return y;
 }
@@ -744,13 +756,24 @@ __device__ __forceinline__ uint32_t bytes_to_01(uint32_t v)
 // (t & 7), or its bit 7 replicated when t >= 8.
 __device__ __forceinline__ uint32_t rule4(const uint32_t lut[4], uint32_t t, uint32_t alive)
 {
-    const uint32_t x = t | (t >> 4);
+    const uint32_t x = __umulhi(t, 1u << 28) + t;   // t | t >> 4 (totals < 16)
     const uint32_t sel = prmt(x, 0u, 0x3120u);   // nibble i = total of cell i
     const uint32_t rd = prmt(lut[0], lut[1], sel);
     const uint32_t rl = prmt(lut[2], lut[3], sel);
     // bit 0 of each byte: the live table's where the cell is alive (alive
     // bytes are 0 or 1), the dead table's elsewhere
     return ((rl & alive) | (rd & ~alive)) & 0x01010101u;
+}
+
+// The same on a fractal whose cells have at most 6 member neighbours: the
+// nibble t + 8 alive (<= 14) picks bit 0 of byte t (dead cell, t
+// neighbours) or, in prmt's sign mode, bit 7 of byte t (live cell, total t)
+// of lut_sparse.
+__device__ __forceinline__ uint32_t rule4_sparse(const uint32_t lut[2], uint32_t t, uint32_t alive)
+{
+    const uint32_t i = alive * 8u + t;
+    const uint32_t x = __umulhi(i, 1u << 28) + i;   // i | i >> 4
+    return prmt(lut[0], lut[1], prmt(x, 0u, 0x3120u)) & 0x01010101u;
 }
 
 // Window of the block of one group: rows r = 0..SG+1, bytes 0..SG+1 of the
@@ -1012,24 +1035,66 @@ __device__ __forceinline__ uint32_t win(const uint32_t *v)
     else return __funnelshift_r(v[P / 4], v[P / 4 + 1], 8 * (P % 4));
 }
 
-// add the 4 bytes w at byte P of a stream whose bytes there are still 0
-template <int P>
-__device__ __forceinline__ void put(uint32_t *S, uint32_t w)
+// Stream of a unit's totals: byte p = 9J + r of the unit comes from group
+// J's word T0 (r < 4), T1 (r = 4..7) or byte 2 of T2 (r = 8), held in
+// R[3J], R[3J + 1], R[3J + 2].  Each stream word is gathered with one prmt
+// from two of them (two prmts where it touches three).
+constexpr int st_reg(int p) { return 3 * (p / 9) + ((p % 9) < 4 ? 0 : ((p % 9) < 8 ? 1 : 2)); }
+constexpr int st_byte(int p) { return (p % 9) < 4 ? p % 9 : ((p % 9) < 8 ? p % 9 - 4 : 2); }
+// the k-th distinct register of stream word W (-1: none)
+constexpr int st_word_reg(int W, int k)
 {
-    if constexpr (P % 4 == 0) S[P / 4] += w;
-    else {
-        S[P / 4] += w << (8 * (P % 4));
-        S[P / 4 + 1] += w >> (32 - 8 * (P % 4));
+    int regs[4] = {-1, -1, -1, -1}, n = 0;
+    for (int i = 0; i < 4; ++i) {
+        const int p = 4 * W + i;
+        if (p >= kUnitCells) break;
+        const int r = st_reg(p);
+        bool seen = false;
+        for (int j = 0; j < n; ++j) seen = seen || regs[j] == r;
+        if (!seen) regs[n++] = r;
     }
+    return regs[k];
+}
+// selector of byte i of word W: its byte in the pair (first reg, second
+// reg) when `pair`, else in (prmt result, third reg); 4 (a zero) past the unit
+constexpr uint32_t st_nibble(int W, int i, bool pair)
+{
+    const int p = 4 * W + i;
+    if (p >= kUnitCells) return 4;
+    const int r = st_reg(p), b = st_byte(p);
+    if (pair) return (uint32_t)(r == st_word_reg(W, 1) ? 4 + b : (r == st_word_reg(W, 0) ? b : 4));
+    return (uint32_t)(r == st_word_reg(W, 2) ? 4 + b : i);
+}
+constexpr uint32_t st_sel(int W, bool pair)
+{
+    return st_nibble(W, 0, pair) | st_nibble(W, 1, pair) << 4 | st_nibble(W, 2, pair) << 8 |
+           st_nibble(W, 3, pair) << 12;
 }
 
-// totals (3x3 sums including the cell) of group J of a unit, added to the
-// unit's stream S at bytes 9J .. 9J+8
+template <int W>
+__device__ __forceinline__ uint32_t stream_word(const uint32_t *R)
+{
+    constexpr int r0 = st_word_reg(W, 0), r1 = st_word_reg(W, 1), r2 = st_word_reg(W, 2);
+    constexpr uint32_t s1 = st_sel(W, true);
+    if constexpr (r1 < 0 && s1 == 0x3210u) return R[r0];
+    else if constexpr (r1 < 0) return prmt(R[r0], 0u, s1);
+    else if constexpr (r2 < 0) return prmt(R[r0], R[r1], s1);
+    else return prmt(prmt(R[r0], R[r1], s1), R[r2], st_sel(W, false));
+}
+
+template <int... W>
+__device__ __forceinline__ void stream_words(const uint32_t *R, uint32_t *S, std::integer_sequence<int, W...>)
+{
+    ((S[W] = stream_word<W>(R)), ...);
+}
+
+// totals (3x3 sums including the cell) of group J of a unit: lids 0..3 in
+// R[3J], 4..7 in R[3J + 1], lid 8 in byte 2 of R[3J + 2]
 template <int J>
-__device__ __forceinline__ void unit_group(const uint32_t *v, const uint32_t *x, uint32_t *S)
+__device__ __forceinline__ void unit_group(const uint32_t *v, const uint32_t *x, uint32_t *R)
 {
     constexpr int b = 9 * J;
-    const uint32_t A = win<b>(v), B = win<b + 4>(v);     // lids 0-3, 4-7
+    const uint32_t A = win<b>(v), B = win<b + 4>(v);     // lids 0-3, 4-7 (bytes 0 or 1)
     const uint32_t P0 = A * 0x010101u;                   // byte 2: l0 + l1 + l2
     const uint32_t P1 = win<b + 3>(v) * 0x010101u;      // byte 2: l3 + l4 + l5
     const uint32_t P2 = win<b + 6>(v) * 0x010101u;      // byte 2: l6 + l7 + l8
@@ -1038,38 +1103,13 @@ __device__ __forceinline__ void unit_group(const uint32_t *v, const uint32_t *x,
     const uint32_t ne8 = tap_byte<tap_src(J, 4)>(v, x), s0 = tap_byte<tap_src(J, 5)>(v, x);
     const uint32_t s1 = tap_byte<tap_src(J, 6)>(v, x), sw4 = tap_byte<tap_src(J, 7)>(v, x);
     // lids 0..3: t0 + N8 + W4 | t0 + l3 + l5 + N8 | t0 + l6 + l7 + W4 | t1 + l1
-    const uint32_t T0 = prmt(P0, P1, 0x6222u) + (prmt(A, B, 0x1630u) & 0xffffff00u) + prmt(B, 0u, 0x4314u) +
-                        w4 * 0x00010001u + n8 * 0x00000101u;
+    // (selector nibble 8: the sign of byte 0 replicated, i.e. 0)
+    R[3 * J] = prmt(P0, P1, 0x6222u) + prmt(A, B, 0x1638u) + prmt(B, 0u, 0x4314u) + w4 * 0x00010001u +
+               n8 * 0x00000101u;
     // lids 4..7: t1 + NE8 + E0 + E2 | t1 + l1 + l7 | t2 + l2 | t2 + l2 + l5
-    const uint32_t T1 = prmt(P1, P2, 0x6622u) + prmt(A, 0u, 0x2214u) + prmt(B, 0u, 0x1434u) + (ne8 + e0 + e2);
+    R[3 * J + 1] = prmt(P1, P2, 0x6622u) + prmt(A, 0u, 0x2214u) + prmt(B, 0u, 0x1434u) + (ne8 + e0 + e2);
     // lid 8 (byte 2): t2 + SW4 + S0 + S1
-    const uint32_t T2 = P2 + ((sw4 + s0 + s1) << 16);
-    put<b>(S, T0);
-    put<b + 4>(S, T1);
-    S[(b + 8) / 4] += prmt(T2, 0u, (0x4444u & ~(0xfu << (4 * ((b + 8) % 4)))) | (2u << (4 * ((b + 8) % 4))));
-}
-
-// store bytes 0..80 of the stream o at ob, where ob - M is word aligned
-// (whole words where they hold only this unit's bytes, bytes elsewhere)
-template <int M>
-__device__ __forceinline__ void store_unit(uint8_t *ob, const uint32_t *o)
-{
-    constexpr int H = (4 - M) & 3;                  // bytes before the first whole word
-    constexpr int NWF = (kUnitCells - H) / 4;       // whole words
-    constexpr int TL = kUnitCells - H - 4 * NWF;    // bytes after them
-#pragma unroll
-    for (int j = 0; j < H; ++j) ob[j] = (uint8_t)(o[0] >> (8 * j));
-#pragma unroll
-    for (int i = 0; i < NWF; ++i) {
-        const int P = H + 4 * i;
-        const uint32_t w = (P % 4 == 0) ? o[P / 4] : __funnelshift_r(o[P / 4], o[P / 4 + 1], 8 * (P % 4));
-        sts32(ob + P, w);
-    }
-#pragma unroll
-    for (int j = 0; j < TL; ++j) {
-        const int P = H + 4 * NWF + j;
-        ob[P] = (uint8_t)(o[P / 4] >> (8 * (P % 4)));
-    }
+    R[3 * J + 2] = P2 + ((sw4 + s0 + s1) << 16);
 }
 
 // external tap cell C, 0 or 1, read from the stage
@@ -1077,8 +1117,7 @@ template <int C>
 __device__ __forceinline__ uint32_t ext_tap(const uint8_t *tin, const uint32_t *e)
 {
     constexpr int g = kXg[C], lid = kXlid[C];
-    const uint32_t o = (g & 1) ? (e[g / 2] >> 16) : (e[g / 2] & 0xffffu);
-    return min((uint32_t)tin[o + lid], 1u);
+    return min((uint32_t)tin[e[g] + lid], 1u);
 }
 
 template <int... C>
@@ -1092,20 +1131,29 @@ struct TapPolicy {
     static constexpr bool kRingInTile = true;   // halo bytes go after the tile's bytes
     static constexpr int NW = (kUnitCells + 3) / 4;   // 21 words per unit
     struct Regs {
-        uint32_t e[kExtGroups / 2];   // byte offsets 9 g of the external groups, two per word
+        uint32_t e[kExtGroups];   // byte offsets 9 g of the unit's external groups
     };
     __device__ static void init(const StepArgs &a, Regs &R)
     {
         const int q = threadIdx.x;
 #pragma unroll
-        for (int k = 0; k < kExtGroups / 2; ++k)
-            R.e[k] = (q < a.nq) ? __ldg(a.tab + (kExtGroups / 2) * q + k) : 0u;
+        for (int k = 0; k < kExtGroups / 2; ++k) {
+            const uint32_t w = (q < a.nq) ? __ldg(a.tab + (kExtGroups / 2) * q + k) : 0u;
+            R.e[2 * k] = w & 0xffffu;
+            R.e[2 * k + 1] = w >> 16;
+        }
     }
     // the all-zero group, after the halo groups (the bulk copy may have
     // written there); `tin` is the tile's first cell in the stage
     __device__ static void fill(const StepArgs &a, uint8_t *tin)
     {
         if (threadIdx.x < 9) tin[9 * a.tapz + threadIdx.x] = 0;
+    }
+    // the tile bytes warp w writes: those of units 32w .. 32w + 31
+    __device__ static void warp_bytes(const StepArgs &a, int w, int *b0, int *b1)
+    {
+        *b0 = kUnitCells * min(32 * w, a.nq);
+        *b1 = kUnitCells * min(32 * w + 32, a.nq);
     }
     __device__ static void scatter(const StepArgs &, const TileIO &, uint8_t *, const uint32_t *, Regs &) {}
 
@@ -1137,26 +1185,42 @@ struct TapPolicy {
         }
         uint32_t x[kExtCells];
         ext_taps(tin, R.e, x, std::make_integer_sequence<int, kExtCells>());
-        uint32_t S[NW];
+        uint32_t T[3 * kUnitGroups];
+        unit_group<0>(v, x, T);
+        unit_group<1>(v, x, T);
+        unit_group<2>(v, x, T);
+        unit_group<3>(v, x, T);
+        unit_group<4>(v, x, T);
+        unit_group<5>(v, x, T);
+        unit_group<6>(v, x, T);
+        unit_group<7>(v, x, T);
+        unit_group<8>(v, x, T);
+        uint32_t o[NW];
+        stream_words(T, o, std::make_integer_sequence<int, NW>());
 #pragma unroll
-        for (int i = 0; i < NW; ++i) S[i] = 0;
-        unit_group<0>(v, x, S);
-        unit_group<1>(v, x, S);
-        unit_group<2>(v, x, S);
-        unit_group<3>(v, x, S);
-        unit_group<4>(v, x, S);
-        unit_group<5>(v, x, S);
-        unit_group<6>(v, x, S);
-        unit_group<7>(v, x, S);
-        unit_group<8>(v, x, S);
-#pragma unroll
-        for (int i = 0; i < NW; ++i) S[i] = rule4(io.rule.lut, S[i], v[i]);
+        for (int i = 0; i < NW; ++i) o[i] = rule4_sparse(io.rule.lut_sparse, o[i], v[i]);
+        // store bytes 0..80 of o at ob: word i of the aligned run from ob - m
+        // holds stream bytes 4i - m .. 4i - m + 3; words 1..19 are the
+        // unit's own, words 0 and 20 are shared with the neighbouring units
+        // unless m = 0 (word 0) or m = 3 (word 20) and are written byte by byte
         uint8_t *ob = io.ostage + io.a_out + kUnitCells * q;
-        switch ((io.a_out + kUnitCells * q) & 3) {
-        case 0: store_unit<0>(ob, S); break;
-        case 1: store_unit<1>(ob, S); break;
-        case 2: store_unit<2>(ob, S); break;
-        default: store_unit<3>(ob, S); break;
+        const uint32_t m = (uint32_t)(io.a_out + kUnitCells * q) & 3u;
+        uint8_t *base = ob - m;
+        const uint32_t sl = 8u * m;
+#pragma unroll
+        for (int i = 1; i < NW - 1; ++i) sts32(base + 4 * i, __funnelshift_l(o[i - 1], o[i], sl));
+        const uint32_t w0 = o[0] << sl, w20 = __funnelshift_l(o[NW - 2], o[NW - 1], sl);
+        if (m == 0) sts32(base, w0);
+        else {
+#pragma unroll
+            for (int j = 1; j < 4; ++j)
+                if ((uint32_t)j >= m) base[j] = (uint8_t)(w0 >> (8 * j));
+        }
+        if (m == 3) sts32(base + 4 * (NW - 1), w20);
+        else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if ((uint32_t)j <= m) base[4 * (NW - 1) + j] = (uint8_t)(w20 >> (8 * j));
         }
     }
 };
@@ -1313,21 +1377,23 @@ __device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, 
 }
 
 // Tile loop of the policies that compute from the input stage itself, with
-// one block barrier per tile.  Tile i is computed into output stage i & 1;
-// then each thread waits for tile i+1's stage and fills its share of it, and
-// the barrier that follows both closes tile i and opens tile i+1.  After it,
-// thread 0 refills tile i's input stage and stores its output stage (the
-// store of tile i-2 from the same output stage has finished reading it
-// before the barrier).
+// one block barrier per tile.  After computing tile i, each warp stores its
+// own bytes of the output stage (a bulk copy of their 16-byte aligned part,
+// plain stores for the ends) and waits for that copy to have read them
+// before it writes the output stage again; then each thread waits for tile
+// i+1's stage and fills its share of it, and the barrier that follows both
+// closes tile i and opens tile i+1.  After it, thread 0 refills tile i's
+// input stage.
 template <bool MULTI, class Pol>
 __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_t *in, uint8_t *out,
                                                  uint8_t *smem, uint64_t *bars, const uint32_t *tab,
                                                  typename Pol::Regs &R)
 {
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t G = gridDim.x;
-    const int ostride = kStagePad + a.tile_bytes;
-    uint8_t *ostage0 = smem + a.off_out + kStagePad;
+    uint8_t *ostage = smem + a.off_out + kStagePad;
+    int wb0, wb1;   // this warp's bytes of a tile
+    Pol::warp_bytes(a, tid >> 5, &wb0, &wb1);
     int64_t Tg = blockIdx.x;
     if (Tg >= a.NT) return;
     uint32_t rv[kRingRegs];
@@ -1358,7 +1424,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
             const int32_t *nrow_n = reinterpret_cast<const int32_t *>(next_stage);
 #pragma unroll
             for (int k = 0; k < kRingRegs; ++k) {
-                const int e = tid + k * nth;
+                const int e = tid + k * blockDim.x;
                 if (e < a.nring) {
                     const uint32_t w0 = __ldg(a.ring + 2 * e);
                     const int32_t tnb = nrow_n[w0 >> 24];
@@ -1367,51 +1433,50 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
             }
             pref = true;
         }
-        uint8_t *ostage = ostage0 + (int)(i & 1) * ostride;
         TileIO io = tile_io(a, t, stage, ostage);
         tile_rule<MULTI>(a, Tg, io.rule);
+        if (lane == 0) bulk_wait_read_all();   // this warp's previous store has read its bytes
+        __syncwarp();
         Pol::compute(a, io, nullptr, tab, R);
+        fence_proxy_async_smem();             // this thread's writes, before the bulk copy reads them
+        __syncwarp();
+        if (wb1 > wb0) {
+            const uintptr_t ostart = (uintptr_t)(t.out + t.T * a.KL);
+            const uintptr_t olo = ostart & ~(uintptr_t)15;
+            const uintptr_t g0 = ostart + wb0, g1 = ostart + wb1;
+            const uintptr_t c0 = (g0 + 15) & ~(uintptr_t)15, c1 = g1 & ~(uintptr_t)15;
+            if (c1 > c0) {
+                if (lane == 0) {
+                    bulk_s2g((void *)c0, ostage + (c0 - olo), (uint32_t)(c1 - c0));
+                    bulk_commit();
+                }
+                const int head = (int)(c0 - g0), tail = (int)(g1 - c1);
+                if (lane < head) *(uint8_t *)(g0 + lane) = ostage[g0 + lane - olo];
+                else if (lane >= 16 && lane < 16 + tail) *(uint8_t *)(c1 + lane - 16) = ostage[c1 + lane - 16 - olo];
+            } else {
+                for (uintptr_t ad = g0 + lane; ad < g1; ad += 32) *(uint8_t *)ad = ostage[ad - olo];
+            }
+        }
         ok = true;
         if (has_next) {
             ok = mbar_wait_bounded(&bars[sn], pn);
             if (ok) fill_stage<MULTI, Pol>(a, tn, next_stage, rv, pref);
         }
-        if (tid == 0) bulk_wait_read_all();
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
             drain_loads(a, bars, i + 1, i + a.nstage - 1);
             break;
         }
-        const uintptr_t ostart = (uintptr_t)(t.out + t.T * a.KL);
-        const uintptr_t oend = ostart + (uintptr_t)a.KL;
-        const uintptr_t olo = ostart & ~(uintptr_t)15;
-        const uintptr_t c0 = (ostart + 15) & ~(uintptr_t)15;
-        const uintptr_t c1 = oend & ~(uintptr_t)15;
         if (tid == 0) {
             fence_proxy_async_smem();
             const int64_t Tr = Tg + a.nstage * G;
             if (Tr < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tr), stage, &bars[s]);
-            if (c1 > c0) {
-                bulk_s2g((void *)c0, ostage + (c0 - olo), (uint32_t)(c1 - c0));
-                bulk_commit();
-            }
-        }
-        const uint8_t *tout = ostage + io.a_out;
-        if (c1 > c0) {
-            const int head = (int)(c0 - ostart), tail = (int)(oend - c1);
-            if (tid < head) *(uint8_t *)(ostart + tid) = tout[tid];
-            else if (tid >= 32 && tid < 32 + tail) {
-                const int j = tid - 32;
-                *(uint8_t *)(c1 + j) = ostage[c1 - olo + j];
-            }
-        } else {
-            for (int64_t l = tid; l < a.KL; l += nth) *(uint8_t *)(ostart + l) = tout[l];
         }
         if (!has_next) break;
         Tg = Tn;
         t = tn;
     }
-    if (tid == 0) bulk_wait_all();
+    if (lane == 0) bulk_wait_all();
 }
 
 // Tile loop of the policies that compute from the box: wait for the tile's
@@ -1562,7 +1627,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
 }
 
 template <int DIM, int MODE, bool MULTI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, MODE == kModeTap ? 3 : 1)
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     using Pol = typename PolicyOf<DIM, MODE>::type;
@@ -1619,6 +1684,13 @@ void make_rule(uint32_t birth, uint32_t survive, Rule *r)
     r->birth = birth;
     r->survive = survive;
     rule_tables(birth, survive, r->lut);
+    // byte j: bit 0 = a dead cell with j live neighbours is born, bit 7 = a
+    // live cell with total j (j - 1 live neighbours) survives
+    uint8_t sp[8];
+    for (int j = 0; j < 8; ++j)
+        sp[j] = (uint8_t)(((birth >> j) & 1u) | (j >= 1 ? ((survive >> (j - 1)) & 1u) << 7 : 0u));
+    r->lut_sparse[0] = sp[0] | sp[1] << 8 | sp[2] << 16 | (uint32_t)sp[3] << 24;
+    r->lut_sparse[1] = sp[4] | sp[5] << 8 | sp[6] << 16 | (uint32_t)sp[7] << 24;
 }
 
 static void fill_args(const fractal *f, StepArgs &a)

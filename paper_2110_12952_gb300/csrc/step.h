@@ -15,6 +15,7 @@ namespace fr {
 struct Rule {
     uint32_t birth, survive;
     uint32_t lut[4];
+    uint32_t lut_sparse[2];   // for cells with at most 6 member neighbours (rule4_sparse)
 };
 
 void make_rule(uint32_t birth, uint32_t survive, Rule *r);
