@@ -1143,11 +1143,12 @@ struct TapPolicy {
             R.e[2 * k + 1] = w >> 16;
         }
     }
-    // the all-zero group, after the halo groups (the bulk copy may have
-    // written there); `tin` is the tile's first cell in the stage
-    __device__ static void fill(const StepArgs &a, uint8_t *tin)
+    // the all-zero group, after the halo groups (whatever was there before),
+    // written by lanes 0..8 of the warp that fills the stage; `tin` is the
+    // tile's first cell in the stage
+    __device__ static void fill(const StepArgs &a, uint8_t *tin, int lane)
     {
-        if (threadIdx.x < 9) tin[9 * a.tapz + threadIdx.x] = 0;
+        if (lane < 9) tin[9 * a.tapz + lane] = 0;
     }
     // the tile bytes warp w writes: those of units 32w .. 32w + 31
     __device__ static void warp_bytes(const StepArgs &a, int w, int *b0, int *b1)
@@ -1326,53 +1327,38 @@ __device__ __forceinline__ TileIO tile_io(const StepArgs &a, const TileRef &t, u
     return io;
 }
 
-// Complete a landed stage for the compute of a ring-in-tile policy: the
-// tile bytes the bulk copy could not cover (unaligned buffer ends), the
-// policy's own bytes and the halo cells, the first kRingRegs per thread
-// from `rv` when they were prefetched.
+// Complete a landed stage for the compute of a ring-in-tile policy, by one
+// warp: the tile bytes the bulk copy could not cover (within 16 bytes of an
+// unaligned end of the instance's buffer), the policy's own bytes and the
+// halo cells; halo entry `lane` comes from `rv` when it was prefetched.
 template <bool MULTI, class Pol>
-__device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, uint8_t *stage,
-                                           const uint32_t *rv, bool pref)
+__device__ __forceinline__ void fill_stage_warp(const StepArgs &a, const TileRef &t, uint8_t *stage, uint32_t rv,
+                                                bool pref)
 {
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = threadIdx.x & 31;
     const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
-    TileIO io = tile_io(a, t, stage, nullptr);
-    uint8_t *data = const_cast<uint8_t *>(io.data);
     const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
     const uintptr_t end = start + (uintptr_t)a.KL;
-    const uintptr_t lo = start & ~(uintptr_t)15;
+    uint8_t *tin = stage + 4 * a.nbrw + kStagePad + (int)(start & 15);
+    // the bulk copy covered [cf, ct)
     const uintptr_t in_lo = ((uintptr_t)t.in + 15) & ~(uintptr_t)15;
     const uintptr_t in_hi = ((uintptr_t)t.in + (uintptr_t)t.cells) & ~(uintptr_t)15;
-    uintptr_t b0 = lo > in_lo ? lo : in_lo;
-    uintptr_t b1 = (end + 15) & ~(uintptr_t)15;
-    if (b1 > in_hi) b1 = in_hi;
-    if (b0 > start || b1 < end) {
-        for (int64_t l = tid; l < a.KL; l += nth) {
-            const uintptr_t ad = start + l;
-            if (ad < b0 || ad >= b1) data[ad - lo] = *(const uint8_t *)ad;
-        }
+    const uintptr_t cf = start > in_lo ? start : in_lo, ct = end < in_hi ? end : in_hi;
+    if (cf >= ct) {
+        for (int64_t l = lane; l < a.KL; l += 32) tin[l] = ((const uint8_t *)start)[l];
+    } else {
+        if ((uintptr_t)lane < cf - start) tin[lane] = ((const uint8_t *)start)[lane];
+        if ((uintptr_t)lane < end - ct) tin[ct - start + lane] = ((const uint8_t *)ct)[lane];
     }
-    uint8_t *tin = data + io.a_in;
-    Pol::fill(a, tin);
-#pragma unroll
-    for (int k = 0; k < kRingRegs; ++k) {
-        const int e = tid + k * nth;
-        if (e < a.nring) {
-            const uint32_t w0 = __ldg(a.ring + 2 * e);
-            uint32_t v = rv[k];
-            if (!pref) {
-                const int32_t tn = nrow[w0 >> 24];
-                v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
-            }
-            tin[w0 & 0xffffff] = v != 0;
+    Pol::fill(a, tin, lane);
+    for (int e = lane; e < a.nring; e += 32) {
+        const uint32_t w0 = __ldg(a.ring + 2 * e);
+        uint32_t v = rv;
+        if (!pref || e != lane) {
+            const int32_t tn = nrow[w0 >> 24];
+            v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
         }
-    }
-    for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
-        const uint32_t w0 = __ldg(a.ring + 2 * e), lw = __ldg(a.ring + 2 * e + 1);
-        const int32_t tn = nrow[w0 >> 24];
-        uint8_t v = 0;
-        if (tn >= 0) v = t.in[(int64_t)tn * a.KL + lw] != 0;
-        tin[w0 & 0xffffff] = v;
+        tin[w0 & 0xffffff] = v != 0;
     }
 }
 
@@ -1380,8 +1366,8 @@ __device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, 
 // one block barrier per tile.  After computing tile i, each warp stores its
 // own bytes of the output stage (a bulk copy of their 16-byte aligned part,
 // plain stores for the ends) and waits for that copy to have read them
-// before it writes the output stage again; then each thread waits for tile
-// i+1's stage and fills its share of it, and the barrier that follows both
+// before it writes the output stage again; every thread waits for tile
+// i+1's stage, the last warp fills it, and the barrier that follows both
 // closes tile i and opens tile i+1.  After it, thread 0 refills tile i's
 // input stage.
 template <bool MULTI, class Pol>
@@ -1389,48 +1375,40 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
                                                  uint8_t *smem, uint64_t *bars, const uint32_t *tab,
                                                  typename Pol::Regs &R)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool filler = warp == (int)(blockDim.x >> 5) - 1;
     const int64_t G = gridDim.x;
     uint8_t *ostage = smem + a.off_out + kStagePad;
     int wb0, wb1;   // this warp's bytes of a tile
-    Pol::warp_bytes(a, tid >> 5, &wb0, &wb1);
+    Pol::warp_bytes(a, warp, &wb0, &wb1);
     int64_t Tg = blockIdx.x;
     if (Tg >= a.NT) return;
-    uint32_t rv[kRingRegs];
-#pragma unroll
-    for (int k = 0; k < kRingRegs; ++k) rv[k] = 0;
+    uint32_t rv = 0;   // prefetched halo value of the next tile (filler lanes)
     TileRef t = resolve<MULTI>(a, in, out, Tg);
     bool ok = mbar_wait_bounded(&bars[0], 0);
-    if (ok) fill_stage<MULTI, Pol>(a, t, smem, rv, false);
+    if (ok && filler) fill_stage_warp<MULTI, Pol>(a, t, smem, rv, false);
     if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
         drain_loads(a, bars, 0, a.nstage - 1);
         return;
     }
+    int s = 0;   // stage of tile i (the block's i-th), the next tile's stage and parity
+    int sn = (a.nstage > 1) ? 1 : 0;
+    uint32_t pn = (sn == 0) ? 1u : 0u;
     for (int64_t i = 0;; ++i) {
-        const int s = (int)(i % a.nstage);
         uint8_t *stage = smem + s * a.stage_bytes;
         const int64_t Tn = Tg + G;
         const bool has_next = Tn < a.NT;
-        const int sn = (int)((i + 1) % a.nstage);
-        const uint32_t pn = (uint32_t)(((i + 1) / a.nstage) & 1);
         uint8_t *next_stage = smem + sn * a.stage_bytes;
         TileRef tn = t;
         if (has_next) tn = resolve<MULTI>(a, in, out, Tn);
-        // the next tile's halo values, when its stage has landed already
-        // (never waited for here): the loads stay in flight during the compute
+        // the next tile's halo value, when its stage has landed already
+        // (never waited for here): the load stays in flight during the compute
         bool pref = false;
-        if (has_next && tid < a.nring && mbar_test(&bars[sn], pn)) {
-            const int32_t *nrow_n = reinterpret_cast<const int32_t *>(next_stage);
-#pragma unroll
-            for (int k = 0; k < kRingRegs; ++k) {
-                const int e = tid + k * blockDim.x;
-                if (e < a.nring) {
-                    const uint32_t w0 = __ldg(a.ring + 2 * e);
-                    const int32_t tnb = nrow_n[w0 >> 24];
-                    rv[k] = (tnb >= 0) ? tn.in[(int64_t)tnb * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
-                }
-            }
+        if (filler && has_next && lane < a.nring && mbar_test(&bars[sn], pn)) {
+            const uint32_t w0 = __ldg(a.ring + 2 * lane);
+            const int32_t tnb = reinterpret_cast<const int32_t *>(next_stage)[w0 >> 24];
+            rv = (tnb >= 0) ? tn.in[(int64_t)tnb * a.KL + __ldg(a.ring + 2 * lane + 1)] : 0u;
             pref = true;
         }
         TileIO io = tile_io(a, t, stage, ostage);
@@ -1441,26 +1419,28 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         fence_proxy_async_smem();             // this thread's writes, before the bulk copy reads them
         __syncwarp();
         if (wb1 > wb0) {
-            const uintptr_t ostart = (uintptr_t)(t.out + t.T * a.KL);
-            const uintptr_t olo = ostart & ~(uintptr_t)15;
-            const uintptr_t g0 = ostart + wb0, g1 = ostart + wb1;
-            const uintptr_t c0 = (g0 + 15) & ~(uintptr_t)15, c1 = g1 & ~(uintptr_t)15;
-            if (c1 > c0) {
+            // ostage[al + j] holds tile byte j; the warp's bytes [wb0, wb1)
+            // are a bulk copy between their first and last 16-byte
+            // boundaries in memory and plain stores around them
+            uint8_t *ob = t.out + t.T * a.KL;
+            const int al = io.a_out;
+            const int head = (16 - ((al + wb0) & 15)) & 15, tail = (al + wb1) & 15;
+            const int n = wb1 - wb0;
+            if (n > head + tail) {
                 if (lane == 0) {
-                    bulk_s2g((void *)c0, ostage + (c0 - olo), (uint32_t)(c1 - c0));
+                    bulk_s2g(ob + wb0 + head, ostage + al + wb0 + head, (uint32_t)(n - head - tail));
                     bulk_commit();
                 }
-                const int head = (int)(c0 - g0), tail = (int)(g1 - c1);
-                if (lane < head) *(uint8_t *)(g0 + lane) = ostage[g0 + lane - olo];
-                else if (lane >= 16 && lane < 16 + tail) *(uint8_t *)(c1 + lane - 16) = ostage[c1 + lane - 16 - olo];
+                if (lane < head) ob[wb0 + lane] = ostage[al + wb0 + lane];
+                else if (lane >= 16 && lane < 16 + tail) ob[wb1 - tail + lane - 16] = ostage[al + wb1 - tail + lane - 16];
             } else {
-                for (uintptr_t ad = g0 + lane; ad < g1; ad += 32) *(uint8_t *)ad = ostage[ad - olo];
+                for (int j = wb0 + lane; j < wb1; j += 32) ob[j] = ostage[al + j];
             }
         }
         ok = true;
         if (has_next) {
             ok = mbar_wait_bounded(&bars[sn], pn);
-            if (ok) fill_stage<MULTI, Pol>(a, tn, next_stage, rv, pref);
+            if (ok && filler) fill_stage_warp<MULTI, Pol>(a, tn, next_stage, rv, pref);
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
@@ -1475,6 +1455,9 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         if (!has_next) break;
         Tg = Tn;
         t = tn;
+        s = sn;
+        sn = (sn + 1 == a.nstage) ? 0 : sn + 1;
+        if (sn == 0) pn ^= 1u;
     }
     if (lane == 0) bulk_wait_all();
 }
@@ -1499,9 +1482,10 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
     bool pref = false;
 
     int64_t i = 0;
-    for (int64_t Tg = blockIdx.x; Tg < a.NT; Tg += G, ++i) {
-        const int s = (int)(i % a.nstage);
-        const uint32_t parity = (uint32_t)((i / a.nstage) & 1);
+    int s = 0;             // stage of the block's i-th tile and the parity of its wait
+    uint32_t parity = 0;
+    for (int64_t Tg = blockIdx.x; Tg < a.NT;
+         Tg += G, ++i, s = (s + 1 == a.nstage) ? 0 : s + 1, parity ^= (s == 0) ? 1u : 0u) {
         uint8_t *stage = smem + s * a.stage_bytes;
         const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
         const bool ok = mbar_wait_bounded(&bars[s], parity);
@@ -1567,8 +1551,8 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
         // this tile is computed
         pref = false;
         if (tid < a.nring && Tg + G < a.NT) {
-            const int sn = (int)((i + 1) % a.nstage);
-            const uint32_t pn = (uint32_t)(((i + 1) / a.nstage) & 1);
+            const int sn = (s + 1 == a.nstage) ? 0 : s + 1;
+            const uint32_t pn = (sn == 0) ? parity ^ 1u : parity;
             if (mbar_test(&bars[sn], pn)) {
                 const TileRef tn_ref = resolve<MULTI>(a, in, out, Tg + G);
                 const int32_t *nrow_n = reinterpret_cast<const int32_t *>(smem + sn * a.stage_bytes);
