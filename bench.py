@@ -301,10 +301,13 @@ def run_ours(args, rank, world, dist):
     alg_bytes = 2.0 * g.cells
     achieved = alg_bytes / (ms / args.steps / 1e3) / 1e9
     workload = workload_config(inst)["workload"]
+    plan = g.plan_info()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_per_launch(workload), "kernel": "step_tma_kernel<2,4>",
+            "traffic": traffic_per_launch(workload),
+            "kernel": f"step_tma_kernel<2,{plan['policy']},false> ({plan['policy_name']} policy)",
             "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_src,
-            "tile_levels": g.tile_levels}
+            "tile_levels": plan["tile_levels"], "launch": {k: plan[k] for k in
+                                                           ("block", "grid", "smem_bytes", "stages", "blocks_per_sm")}}
 
     extra = {}
     # end-to-end through the public API from pinned host buffers

@@ -177,6 +177,16 @@ int fractal_run_host(fractal_t *f, const uint8_t *host_in, uint8_t *host_out,
 int fractal_set_tile_levels(fractal_t *f, int levels);
 int fractal_get_tile_levels(const fractal_t *f, int *levels);
 
+/* Launch plan of fractal_step for this handle (built, with its
+ * allocations, if it does not exist yet, as by fractal_get_tile_levels).
+ * info[0..n-1] receives, in order: the policy (0: cell by cell, 3 or 4:
+ * groups of s^G x s^G cells, 9: 2D groups of 9 cells in a shared-memory
+ * box, 10: the triangle's 81-cell units with taps), the tile depth L,
+ * threads per block, blocks per launch, dynamic shared memory bytes per
+ * block, input pipeline stages, and resident blocks per SM.  1 <= n <= 7,
+ * else FR_EINVAL. */
+int fractal_plan_info(const fractal_t *f, int32_t *info, int n);
+
 /* Autotuner of fractal_step: times one generation from in_dev into out_dev
  * (both k^r bytes; out_dev is overwritten) for each candidate tile depth
  * (the deepest whose shared-memory layout fits, and the three below), keeps

@@ -48,6 +48,7 @@ SIGNATURES = {
     "fractal_run_host": (c_int, [c_fp, c_vp, c_vp, c_i64, c_u32, c_u32, c_vp]),
     "fractal_set_tile_levels": (c_int, [c_fp, c_int]),
     "fractal_get_tile_levels": (c_int, [c_fp, ctypes.POINTER(c_int)]),
+    "fractal_plan_info": (c_int, [c_fp, ctypes.POINTER(ctypes.c_int32), c_int]),
     "fractal_sync": (c_int, [c_vp]),
     "fractal_check": (c_int, [c_fp]),
     "fractal_step_noalloc": (c_int, [c_fp, c_vp, c_vp, c_i64, c_u32, c_u32, c_vp]),

@@ -191,6 +191,19 @@ extern "C" int fractal_get_tile_levels(const fractal_t *f, int *levels)
     return FR_OK;
 }
 
+extern "C" int fractal_plan_info(const fractal_t *f, int32_t *info, int n)
+{
+    g_err.clear();
+    if (!f || !info) return fail(FR_EINVAL, "fractal_plan_info: NULL argument");
+    if (n < 1 || n > 7) return fail(FR_EINVAL, "fractal_plan_info: n must be in [1, 7]");
+    int rc = ensure_step_plan(const_cast<fractal_t *>(f));
+    if (rc) return rc;
+    const StepPlan &p = f->plan;
+    const int32_t v[7] = {p.mode, p.L, p.block, p.grid, p.smem, p.nstage, p.per_sm};
+    for (int i = 0; i < n; ++i) info[i] = v[i];
+    return FR_OK;
+}
+
 static bool overlap(const void *a, const void *b, int64_t n)
 {
     const uint8_t *x = (const uint8_t *)a, *y = (const uint8_t *)b;

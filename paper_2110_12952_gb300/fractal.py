@@ -156,6 +156,17 @@ class Fractal:
     def tile_levels(self, levels: int):
         self._check(self._lib.fractal_set_tile_levels(self._h, int(levels)))
 
+    POLICIES = {0: "cell", 3: "group3", 4: "group4", 9: "quad", 10: "tap"}
+
+    def plan_info(self) -> dict:
+        """The step's launch plan (``fractal_plan_info``)."""
+        v = (ctypes.c_int32 * 7)()
+        self._check(self._lib.fractal_plan_info(self._h, v, 7))
+        keys = ("policy", "tile_levels", "block", "grid", "smem_bytes", "stages", "blocks_per_sm")
+        d = dict(zip(keys, (int(x) for x in v)))
+        d["policy_name"] = self.POLICIES.get(d["policy"], str(d["policy"]))
+        return d
+
     def autotune(self, state: torch.Tensor, out: torch.Tensor | None = None, rule=None,
                  stream=None) -> int:
         """Pick the fastest tile depth on these buffers (``fractal_autotune``);

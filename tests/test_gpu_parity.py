@@ -340,6 +340,25 @@ def test_full_size_bb_triangle_r16(P):
 
 # ------------------------------------------------------------ error paths
 
+def test_plan_info(P):
+    import ctypes
+    g = gpu_fr(P, W.TRIANGLE, 12)
+    g.tile_levels = 8
+    info = g.plan_info()
+    # 81 units of 81 cells per tile of 3^8 cells: 96 threads, two input stages
+    assert info["policy_name"] == "tap" and info["tile_levels"] == 8
+    assert info["block"] == 96 and info["stages"] == 2
+    assert 1 <= info["grid"] <= 3 ** 4 and info["smem_bytes"] > 3 ** 8 and info["blocks_per_sm"] >= 1
+    g.tile_levels = 3   # too shallow for 81-cell units
+    assert g.plan_info()["policy_name"] != "tap"
+    c = gpu_fr(P, W.CARPET, 5)
+    assert c.plan_info()["policy_name"] in ("group3", "cell")
+    arr = (ctypes.c_int32 * 8)()
+    assert g._lib.fractal_plan_info(g._h, arr, 0) != 0
+    assert g._lib.fractal_plan_info(g._h, arr, 8) != 0
+    assert g._lib.fractal_plan_info(g._h, arr, 2) == 0 and arr[1] == 3
+
+
 def test_errors(P):
     from paper_2110_12952_gb300.capi import FractalError
     with pytest.raises(FractalError, match="EINVAL"):
