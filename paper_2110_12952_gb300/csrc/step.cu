@@ -1611,7 +1611,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
 }
 
 template <int DIM, int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, MODE == kModeTap ? 3 : 1)
+__global__ void __launch_bounds__(256, MODE == kModeTap ? 3 : 4)
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     using Pol = typename PolicyOf<DIM, MODE>::type;
