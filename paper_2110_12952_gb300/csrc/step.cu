@@ -52,6 +52,7 @@
 #include "handle.h"
 #include "step.h"
 #include "tma.cuh"
+#include "rows_layout.h"
 
 namespace fr {
 
@@ -139,7 +140,7 @@ static int group_levels(const fractal *f)
     return 0;
 }
 
-enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10 };
+enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10, kModeRows0 = 11, kModeRows1 = 12 };
 
 // ---- tap mode: the Sierpinski triangle with offsets (0,0), (1,0), (0,1)
 // A level-2 group is 9 cells (lid 0..8 at kPosX/kPosY) filling a 4x4 block.
@@ -353,10 +354,124 @@ static TapTables tap_tables(const fractal *f, int L)
     return t;
 }
 
+// ---- rows mode: the carpet and the Vicsek fractal (see rows_layout.h)
+static int rows_preset_of(const fractal *f)
+{
+    if (f->dim != 2 || f->s != 3) return -1;
+    auto same = [&](int k, const int *ox, const int *oy) {
+        if (f->k != k) return false;
+        for (int j = 0; j < k; ++j)
+            if (f->offsets[2 * j] != ox[j] || f->offsets[2 * j + 1] != oy[j]) return false;
+        return true;
+    };
+    if (same(RowsPreset<0>::k, RowsPreset<0>::ox, RowsPreset<0>::oy)) return 0;
+    if (same(RowsPreset<1>::k, RowsPreset<1>::ox, RowsPreset<1>::oy)) return 1;
+    return -1;
+}
+
+// Tables of rows mode for tile depth L (>= 2): per unit (level-2 subtree of
+// the tile), the byte offsets (uint16, two per word) of its 8 neighbouring
+// units in the order of frame_dir, from the tile's first cell in the stage:
+// units of the tile at S u (S = rp_stride), halo units of neighbouring tiles
+// at S (NU + h), an all-zero unit after them; and the halo bytes to fetch per
+// tile (ring entries as in tap mode).
+struct RowsTables {
+    int NU = 0, H = 0;
+    std::vector<uint32_t> words;   // NU * 4
+    std::vector<uint32_t> ring;
+    bool ok = false;
+};
+
+template <int P>
+static RowsTables rows_tables(const fractal *f, int L)
+{
+    RowsTables t;
+    constexpr int K = RowsPreset<P>::k, NB = K * K, S = rp_stride<P>();
+    if (rows_preset_of(f) != P || L < 2) return t;
+    int side = 1, NU = 1;
+    for (int i = 0; i < L - 2; ++i) {
+        side *= 3;
+        NU *= K;
+    }
+    t.NU = NU;
+    std::vector<int> M((size_t)side * side, -1);
+    std::vector<int> ux(NU), uy(NU);
+    for (int q = 0; q < NU; ++q) {
+        int c[3];
+        host_lambda(f, q, L - 2, c);
+        ux[q] = c[0];
+        uy[q] = c[1];
+        M[(size_t)c[1] * side + c[0]] = q;
+    }
+    // the unit layout against the fractal's own lambda
+    for (int q = 0; q < NU; ++q)
+        for (int u = 0; u < NB; ++u) {
+            int c[3];
+            host_lambda(f, (int64_t)NB * q + u, L, c);
+            if (c[0] != 9 * ux[q] + rp_x<P>(u) || c[1] != 9 * uy[q] + rp_y<P>(u)) return t;
+        }
+    uint64_t dir_bytes[8] = {};   // per direction: the unit bytes some frame cell reads
+    for (int fr = 0; fr < kFrame; ++fr)
+        if (frame_byte<P>(fr) >= 0) dir_bytes[frame_dir(fr)] |= 1ull << frame_byte<P>(fr);
+    std::map<std::pair<int, int>, int> slot_of;   // (tile-table slot, unit there) -> halo unit
+    std::vector<std::pair<int, int>> slots;
+    std::vector<uint64_t> bytes_read;
+    std::vector<int> nb((size_t)NU * 8);
+    for (int q = 0; q < NU; ++q)
+        for (int d = 0; d < 8; ++d) {
+            const int d9 = d < 4 ? d : d + 1;
+            int nx = ux[q] + d9 % 3 - 1, ny = uy[q] + d9 / 3 - 1;
+            const int tdx = nx < 0 ? -1 : (nx >= side ? 1 : 0), tdy = ny < 0 ? -1 : (ny >= side ? 1 : 0);
+            nx = (nx + side) % side;
+            ny = (ny + side) % side;
+            const int gn = M[(size_t)ny * side + nx];
+            int v = -2;   // -2: the zero unit
+            if (gn >= 0 && dir_bytes[d]) {
+                if (tdx == 0 && tdy == 0) v = gn;
+                else {
+                    const int t9 = (tdx + 1) + 3 * (tdy + 1);
+                    const int tslot = t9 < 4 ? t9 : t9 - 1;
+                    auto key = std::make_pair(tslot, gn);
+                    auto it = slot_of.find(key);
+                    if (it == slot_of.end()) {
+                        it = slot_of.emplace(key, (int)slots.size()).first;
+                        slots.push_back(key);
+                        bytes_read.push_back(0);
+                    }
+                    bytes_read[it->second] |= dir_bytes[d];
+                    v = -100 - it->second;
+                }
+            }
+            nb[(size_t)q * 8 + d] = v;
+        }
+    t.H = (int)slots.size();
+    const int64_t zero = NU + t.H;
+    if ((int64_t)S * zero + NB >= 65536) return t;
+    t.words.assign((size_t)NU * 4, 0);
+    for (int q = 0; q < NU; ++q)
+        for (int d = 0; d < 8; ++d) {
+            const int v = nb[(size_t)q * 8 + d];
+            const uint32_t off = (v == -2) ? (uint32_t)(S * zero)
+                                 : (v <= -100 ? (uint32_t)(S * (NU + (-100 - v))) : (uint32_t)(S * v));
+            t.words[(size_t)q * 4 + d / 2] |= off << (16 * (d % 2));
+        }
+    // only the halo bytes some frame cell reads are staged
+    for (int hs = 0; hs < t.H; ++hs)
+        for (int b = 0; b < NB; ++b) {
+            if (!((bytes_read[hs] >> b) & 1u)) continue;
+            t.ring.push_back((uint32_t)(S * (NU + hs) + b) | ((uint32_t)slots[hs].first << 24));
+            t.ring.push_back((uint32_t)(NB * slots[hs].second + b));
+        }
+    t.ok = true;
+    return t;
+}
+
 struct Geometry {
     int mode, G, xoff, halo;
     int64_t B, Px, Py, planes;
     int64_t box_bytes, tab_entries, block;
+    int64_t halo_bytes;   // stage bytes after the tile (ring-in-tile policies)
+    int64_t data_bytes;   // if > 0: stage data bytes of a policy with padded units
 };
 
 static int64_t odd_words(int64_t px)
@@ -375,6 +490,8 @@ static Geometry plan_geometry(const fractal *f, int L)
     g.block = 256;
     const bool grp = g.G > 0 && L >= g.G && ipow(f->k, g.G) <= kMaxGroup;
     g.halo = 0;
+    g.halo_bytes = 0;
+    g.data_bytes = 0;
     if (grp && is_triangle(f) && L >= 4 && ipow(f->k, L - 4) <= 256) {
         const TapTables t = tap_tables(f, L);
         if (t.ok) {
@@ -382,7 +499,23 @@ static Geometry plan_geometry(const fractal *f, int L)
             g.Px = g.Py = g.planes = 0;
             g.tab_entries = 0;   // the unit tables live in registers
             g.halo = t.H;
+            g.halo_bytes = 9 * (t.H + 1);
             g.block = std::max<int64_t>(64, ((int64_t)t.NQ + 31) / 32 * 32);
+            g.box_bytes = 0;
+            return g;
+        }
+    }
+    const int rp = rows_preset_of(f);
+    if (rp >= 0 && L >= 2 && ipow(f->k, L - 2) <= 256) {
+        const RowsTables t = rp == 0 ? rows_tables<0>(f, L) : rows_tables<1>(f, L);
+        if (t.ok) {
+            g.mode = rp == 0 ? kModeRows0 : kModeRows1;
+            g.Px = g.Py = g.planes = 0;
+            g.tab_entries = 0;   // the unit tables live in registers
+            g.halo = t.H;
+            g.halo_bytes = (int64_t)f->k * f->k * (t.H + 1);
+            g.data_bytes = (rp == 0) ? (int64_t)rp_stride<0>() * (t.NU + t.H + 1) : 0;
+            g.block = std::max<int64_t>(64, ((int64_t)t.NU + 31) / 32 * 32);
             g.box_bytes = 0;
             return g;
         }
@@ -428,10 +561,10 @@ static Layout plan_layout(const fractal *f, int L)
     Layout y;
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
-    y.nstage = (g.mode == kModeQuad || g.mode == kModeTap) ? 2 : nstages();
+    y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1) ? 2 : nstages();
     // slack: 16-byte rounding of the bulk copy, whole-word reads and writes
     // past the tile's last cell; tap mode: halo and zero groups
-    y.tile_bytes = round16(KL + 64 + (g.mode == kModeTap ? 9 * (g.halo + 1) : 0));
+    y.tile_bytes = round16((g.data_bytes > 0 ? g.data_bytes : KL + g.halo_bytes) + 64);
     y.stage_bytes = 4 * nbr_width(f->dim) + kStagePad + y.tile_bytes;
     int64_t off = y.nstage * y.stage_bytes;
     y.off_bar = off;
@@ -583,6 +716,13 @@ int ensure_step_plan(fractal *f)
         p.nq = t.NQ;
         tab = t.words;
         ring = t.ring;
+    } else if (p.mode == kModeRows0 || p.mode == kModeRows1) {
+        const RowsTables t = p.mode == kModeRows0 ? rows_tables<0>(f, L) : rows_tables<1>(f, L);
+        p.KG = f->k * f->k;
+        p.tapz = t.NU + t.H;
+        p.nq = t.NU;
+        tab = t.words;
+        ring = t.ring;
     } else {
         // local lambda -> padded box offset; occupancy of the interior
         std::vector<uint32_t> pos(p.KL);
@@ -714,6 +854,8 @@ int ensure_step_plan(fractal *f)
     if (dim == 3) rc = configure<3, kModeCell>(p, f->num_sms);
     else if (p.mode == kModeQuad) rc = configure<2, kModeQuad>(p, f->num_sms);
     else if (p.mode == kModeTap) rc = configure<2, kModeTap>(p, f->num_sms);
+    else if (p.mode == kModeRows0) rc = configure<2, kModeRows0>(p, f->num_sms);
+    else if (p.mode == kModeRows1) rc = configure<2, kModeRows1>(p, f->num_sms);
     else if (p.mode == kModeGroup4) rc = configure<2, kModeGroup4>(p, f->num_sms);
     else if (p.mode == kModeGroup3) rc = configure<2, kModeGroup3>(p, f->num_sms);
     else rc = configure<2, kModeCell>(p, f->num_sms);
@@ -1129,6 +1271,7 @@ __device__ __forceinline__ void ext_taps(const uint8_t *tin, const uint32_t *e, 
 
 struct TapPolicy {
     static constexpr bool kRingInTile = true;   // halo bytes go after the tile's bytes
+    static constexpr int kUnitStride = 0;       // the tile's bytes as one copy
     static constexpr int NW = (kUnitCells + 3) / 4;   // 21 words per unit
     struct Regs {
         uint32_t e[kExtGroups];   // byte offsets 9 g of the unit's external groups
@@ -1226,6 +1369,10 @@ struct TapPolicy {
     }
 };
 
+}  // namespace fr
+#include "rows.cuh"
+namespace fr {
+
 template <int DIM, int MODE>
 struct PolicyOf;
 template <int DIM>
@@ -1238,6 +1385,10 @@ template <>
 struct PolicyOf<2, kModeQuad> { using type = QuadPolicy; };
 template <>
 struct PolicyOf<2, kModeTap> { using type = TapPolicy; };
+template <>
+struct PolicyOf<2, kModeRows0> { using type = RowsPolicy<0>; };
+template <>
+struct PolicyOf<2, kModeRows1> { using type = RowsPolicy<1>; };
 
 // A tile of the launch resolved to its instance's buffers, table and rule.
 struct TileRef {
@@ -1327,37 +1478,88 @@ __device__ __forceinline__ TileIO tile_io(const StepArgs &a, const TileRef &t, u
     return io;
 }
 
-// Complete a landed stage for the compute of a ring-in-tile policy, by one
-// warp: the tile bytes the bulk copy could not cover (within 16 bytes of an
-// unaligned end of the instance's buffer), the policy's own bytes and the
-// halo cells; halo entry `lane` comes from `rv` when it was prefetched.
+// Issue the copies of a tile into a stage, by all lanes of one warp: one
+// bulk copy of the tile's bytes, or (policies with padded units) one per
+// unit into its slot.  A unit source that is not 16-byte aligned is copied
+// with plain loads and stores before the stage's mbarrier is armed.
 template <bool MULTI, class Pol>
-__device__ __forceinline__ void fill_stage_warp(const StepArgs &a, const TileRef &t, uint8_t *stage, uint32_t rv,
-                                                bool pref)
+__device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t, uint8_t *stage, uint64_t *bar)
 {
     const int lane = threadIdx.x & 31;
+    if constexpr (Pol::kUnitStride == 0) {
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            issue_tile(a, t, stage, bar);
+        }
+    } else {
+        constexpr int S = Pol::kUnitStride, NB = Pol::NB;
+        const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
+        uint8_t *data = stage + row_bytes + kStagePad;
+        const uint8_t *src = t.in + t.T * a.KL;
+        const bool al = ((uintptr_t)src & 15) == 0;
+        if (!al) {
+            for (int u = lane; u < a.nq; u += 32)
+                for (int b = 0; b < NB; ++b) data[S * u + b] = src[NB * u + b];
+            __threadfence_block();
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, row_bytes + (al ? (uint32_t)(a.nq * NB) : 0u));
+            bulk_g2s(stage, t.nbr + t.T * a.nbrw, row_bytes, bar);
+        }
+        __syncwarp();
+        if (al)
+            for (int u = lane; u < a.nq; u += 32) bulk_g2s(data + S * u, src + NB * u, NB, bar);
+    }
+}
+
+// Complete a landed stage for the compute of a ring-in-tile policy.  The
+// last warp writes the tile bytes the bulk copy could not cover (within 16
+// bytes of an unaligned end of the instance's buffer) and the policy's own
+// bytes; every thread writes its share of the halo cells, entries tid + k *
+// blockDim for k < kRingRegs from `rv` when they were prefetched.
+template <bool MULTI, class Pol>
+__device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, uint8_t *stage, bool filler,
+                                           const uint32_t *rv, bool pref)
+{
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
     const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
     const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
-    const uintptr_t end = start + (uintptr_t)a.KL;
-    uint8_t *tin = stage + 4 * a.nbrw + kStagePad + (int)(start & 15);
-    // the bulk copy covered [cf, ct)
-    const uintptr_t in_lo = ((uintptr_t)t.in + 15) & ~(uintptr_t)15;
-    const uintptr_t in_hi = ((uintptr_t)t.in + (uintptr_t)t.cells) & ~(uintptr_t)15;
-    const uintptr_t cf = start > in_lo ? start : in_lo, ct = end < in_hi ? end : in_hi;
-    if (cf >= ct) {
-        for (int64_t l = lane; l < a.KL; l += 32) tin[l] = ((const uint8_t *)start)[l];
-    } else {
-        if ((uintptr_t)lane < cf - start) tin[lane] = ((const uint8_t *)start)[lane];
-        if ((uintptr_t)lane < end - ct) tin[ct - start + lane] = ((const uint8_t *)ct)[lane];
-    }
-    Pol::fill(a, tin, lane);
-    for (int e = lane; e < a.nring; e += 32) {
-        const uint32_t w0 = __ldg(a.ring + 2 * e);
-        uint32_t v = rv;
-        if (!pref || e != lane) {
-            const int32_t tn = nrow[w0 >> 24];
-            v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+    uint8_t *tin = stage + 4 * a.nbrw + kStagePad + (Pol::kUnitStride ? 0 : (int)(start & 15));
+    if (filler && Pol::kUnitStride) {
+        Pol::fill(a, tin, lane);
+    } else if (filler) {
+        // the bulk copy covered [cf, ct)
+        const uintptr_t end = start + (uintptr_t)a.KL;
+        const uintptr_t in_lo = ((uintptr_t)t.in + 15) & ~(uintptr_t)15;
+        const uintptr_t in_hi = ((uintptr_t)t.in + (uintptr_t)t.cells) & ~(uintptr_t)15;
+        const uintptr_t cf = start > in_lo ? start : in_lo, ct = end < in_hi ? end : in_hi;
+        if (cf >= ct) {
+            for (int64_t l = lane; l < a.KL; l += 32) tin[l] = ((const uint8_t *)start)[l];
+        } else {
+            if ((uintptr_t)lane < cf - start) tin[lane] = ((const uint8_t *)start)[lane];
+            if ((uintptr_t)lane < end - ct) tin[ct - start + lane] = ((const uint8_t *)ct)[lane];
         }
+        Pol::fill(a, tin, lane);
+    }
+#pragma unroll
+    for (int k = 0; k < kRingRegs; ++k) {
+        const int e = tid + k * nth;
+        if (e < a.nring) {
+            const uint32_t w0 = __ldg(a.ring + 2 * e);
+            uint32_t v = rv[k];
+            if (!pref) {
+                const int32_t tn = nrow[w0 >> 24];
+                v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+            }
+            tin[w0 & 0xffffff] = v != 0;
+        }
+    }
+    for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
+        const uint32_t w0 = __ldg(a.ring + 2 * e);
+        const int32_t tn = nrow[w0 >> 24];
+        const uint32_t v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
         tin[w0 & 0xffffff] = v != 0;
     }
 }
@@ -1367,7 +1569,7 @@ __device__ __forceinline__ void fill_stage_warp(const StepArgs &a, const TileRef
 // own bytes of the output stage (a bulk copy of their 16-byte aligned part,
 // plain stores for the ends) and waits for that copy to have read them
 // before it writes the output stage again; every thread waits for tile
-// i+1's stage, the last warp fills it, and the barrier that follows both
+// i+1's stage and fills its share of it, and the barrier that follows both
 // closes tile i and opens tile i+1.  After it, thread 0 refills tile i's
 // input stage.
 template <bool MULTI, class Pol>
@@ -1383,10 +1585,12 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
     Pol::warp_bytes(a, warp, &wb0, &wb1);
     int64_t Tg = blockIdx.x;
     if (Tg >= a.NT) return;
-    uint32_t rv = 0;   // prefetched halo value of the next tile (filler lanes)
+    uint32_t rv[kRingRegs];   // prefetched halo values of the next tile
+#pragma unroll
+    for (int k = 0; k < kRingRegs; ++k) rv[k] = 0;
     TileRef t = resolve<MULTI>(a, in, out, Tg);
     bool ok = mbar_wait_bounded(&bars[0], 0);
-    if (ok && filler) fill_stage_warp<MULTI, Pol>(a, t, smem, rv, false);
+    if (ok) fill_stage<MULTI, Pol>(a, t, smem, filler, rv, false);
     if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
         drain_loads(a, bars, 0, a.nstage - 1);
@@ -1402,23 +1606,42 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         uint8_t *next_stage = smem + sn * a.stage_bytes;
         TileRef tn = t;
         if (has_next) tn = resolve<MULTI>(a, in, out, Tn);
-        // the next tile's halo value, when its stage has landed already
-        // (never waited for here): the load stays in flight during the compute
+        // the next tile's halo values, when its stage has landed already
+        // (never waited for here): the loads stay in flight during the compute
         bool pref = false;
-        if (filler && has_next && lane < a.nring && mbar_test(&bars[sn], pn)) {
-            const uint32_t w0 = __ldg(a.ring + 2 * lane);
-            const int32_t tnb = reinterpret_cast<const int32_t *>(next_stage)[w0 >> 24];
-            rv = (tnb >= 0) ? tn.in[(int64_t)tnb * a.KL + __ldg(a.ring + 2 * lane + 1)] : 0u;
+        if (has_next && tid < a.nring && mbar_test(&bars[sn], pn)) {
+            const int32_t *nrow_n = reinterpret_cast<const int32_t *>(next_stage);
+#pragma unroll
+            for (int k = 0; k < kRingRegs; ++k) {
+                const int e = tid + k * (int)blockDim.x;
+                if (e < a.nring) {
+                    const uint32_t w0 = __ldg(a.ring + 2 * e);
+                    const int32_t tnb = nrow_n[w0 >> 24];
+                    rv[k] = (tnb >= 0) ? tn.in[(int64_t)tnb * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+                }
+            }
             pref = true;
         }
         TileIO io = tile_io(a, t, stage, ostage);
         tile_rule<MULTI>(a, Tg, io.rule);
-        if (lane == 0) bulk_wait_read_all();   // this warp's previous store has read its bytes
+        if (Pol::kUnitStride || lane == 0) bulk_wait_read_all();   // the previous store has read its bytes
         __syncwarp();
         Pol::compute(a, io, nullptr, tab, R);
         fence_proxy_async_smem();             // this thread's writes, before the bulk copy reads them
         __syncwarp();
-        if (wb1 > wb0) {
+        if constexpr (Pol::kUnitStride) {
+            // each thread stores its own unit
+            if (tid < a.nq) {
+                uint8_t *dst = t.out + t.T * a.KL + (int64_t)Pol::NB * tid;
+                const uint8_t *so = ostage + Pol::kUnitStride * tid;
+                if (((uintptr_t)dst & 15) == 0) {
+                    bulk_s2g(dst, so, Pol::NB);
+                    bulk_commit();
+                } else {
+                    for (int b = 0; b < Pol::NB; ++b) dst[b] = so[b];
+                }
+            }
+        } else if (wb1 > wb0) {
             // ostage[al + j] holds tile byte j; the warp's bytes [wb0, wb1)
             // are a bulk copy between their first and last 16-byte
             // boundaries in memory and plain stores around them
@@ -1440,17 +1663,16 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         ok = true;
         if (has_next) {
             ok = mbar_wait_bounded(&bars[sn], pn);
-            if (ok && filler) fill_stage_warp<MULTI, Pol>(a, tn, next_stage, rv, pref);
+            if (ok) fill_stage<MULTI, Pol>(a, tn, next_stage, filler, rv, pref);
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
             drain_loads(a, bars, i + 1, i + a.nstage - 1);
             break;
         }
-        if (tid == 0) {
-            fence_proxy_async_smem();
+        if (warp == 0) {
             const int64_t Tr = Tg + a.nstage * G;
-            if (Tr < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tr), stage, &bars[s]);
+            if (Tr < a.NT) issue_stage<MULTI, Pol>(a, resolve<MULTI>(a, in, out, Tr), stage, &bars[s]);
         }
         if (!has_next) break;
         Tg = Tn;
@@ -1459,7 +1681,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         sn = (sn + 1 == a.nstage) ? 0 : sn + 1;
         if (sn == 0) pn ^= 1u;
     }
-    if (lane == 0) bulk_wait_all();
+    if (Pol::kUnitStride || lane == 0) bulk_wait_all();
 }
 
 // Tile loop of the policies that compute from the box: wait for the tile's
@@ -1611,7 +1833,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
 }
 
 template <int DIM, int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, MODE == kModeTap ? 3 : 4)
+__global__ void __launch_bounds__(256, MODE == kModeTap || MODE == kModeRows0 || MODE == kModeRows1 ? 3 : 4)
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     using Pol = typename PolicyOf<DIM, MODE>::type;
@@ -1625,6 +1847,16 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
     if (tid == 0) {
         for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
         fence_proxy_async_smem();
+    }
+    if constexpr (Pol::kRingInTile) {
+        if (tid < 32) {
+            __syncwarp();
+            for (int s = 0; s < a.nstage; ++s) {
+                const int64_t Tg = blockIdx.x + s * G;
+                if (Tg < a.NT) issue_stage<MULTI, Pol>(a, resolve<MULTI>(a, in, out, Tg), smem + s * a.stage_bytes, &bars[s]);
+            }
+        }
+    } else if (tid == 0) {
         for (int s = 0; s < a.nstage; ++s) {
             const int64_t Tg = blockIdx.x + s * G;
             if (Tg < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tg), smem + s * a.stage_bytes, &bars[s]);
@@ -1725,6 +1957,10 @@ static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t
         step_tma_kernel<2, kModeQuad, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeTap)
         step_tma_kernel<2, kModeTap, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (p.mode == kModeRows0)
+        step_tma_kernel<2, kModeRows0, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (p.mode == kModeRows1)
+        step_tma_kernel<2, kModeRows1, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup4)
         step_tma_kernel<2, kModeGroup4, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup3)

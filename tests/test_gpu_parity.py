@@ -157,17 +157,27 @@ def test_triangle_many_tiles_per_cta(P, L):
     assert np.array_equal(g.step(x, steps=2).cpu().numpy(), o.step(init, steps=2)), f"L={L}"
 
 
-@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 7, 8, 9])
-def test_triangle_nonbinary_input_every_depth(P, L):
+@pytest.mark.parametrize("fam,r,L", [(W.TRIANGLE, 12, L) for L in range(2, 10)] +
+                         [(W.CARPET, 6, L) for L in range(1, 6)] + [(W.VICSEK, 7, L) for L in range(1, 6)])
+def test_nonbinary_input_every_depth(P, fam, r, L):
     # any nonzero byte is alive: the first generation must read 0..255 as
-    # 0/1 wherever a cell is read (own cells, taps, halo)
-    fam, r = W.TRIANGLE, 12
+    # 0/1 wherever a cell is read (own cells, taps, frames, halo)
     g, o = gpu_fr(P, fam, r), ora(fam, r)
     rng = np.random.default_rng(100 + L)
     raw = (rng.integers(0, 2, size=g.cells) * rng.integers(1, 256, size=g.cells)).astype(np.uint8)
     g.tile_levels = L
-    out = g.step(torch.from_numpy(raw).cuda(), steps=1)
-    assert np.array_equal(out.cpu().numpy(), o.step(raw, steps=1)), f"L={L}"
+    out = g.step(torch.from_numpy(raw).cuda(), steps=1, rule=rule_of(fam))
+    assert np.array_equal(out.cpu().numpy(), o.step(raw, rule=oracle_rule(fam), steps=1)), f"L={L}"
+
+
+@pytest.mark.parametrize("fam,r,L", [(W.CARPET, 8, L) for L in (2, 3, 4)] + [(W.VICSEK, 9, L) for L in (2, 3, 4, 5)])
+def test_rows_policy_many_tiles_per_cta(P, fam, r, L):
+    # thousands of tiles per launch: every CTA reuses its stages many times
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(9, 0.5)
+    g.tile_levels = L
+    out = g.step(torch.from_numpy(init).cuda(), steps=3, rule=rule_of(fam))
+    assert np.array_equal(out.cpu().numpy(), o.step(init, rule=oracle_rule(fam), steps=3)), f"L={L}"
 
 
 def test_autotune_keeps_parity(P):
@@ -352,6 +362,10 @@ def test_plan_info(P):
     g.tile_levels = 3   # too shallow for 81-cell units
     assert g.plan_info()["policy_name"] != "tap"
     c = gpu_fr(P, W.CARPET, 5)
+    c.tile_levels = 4
+    ci = c.plan_info()
+    assert ci["policy_name"] == "rows_carpet" and ci["block"] == 64   # 8^2 units of 64 cells
+    c.tile_levels = 1
     assert c.plan_info()["policy_name"] in ("group3", "cell")
     arr = (ctypes.c_int32 * 8)()
     assert g._lib.fractal_plan_info(g._h, arr, 0) != 0
