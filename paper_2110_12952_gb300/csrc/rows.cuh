@@ -306,10 +306,18 @@ struct RowsPolicy {
         unit_band<P, 2>(tin, R.e, io.rule, v, x, r, t, o, std::make_integer_sequence<int, NE>(),
                         std::make_integer_sequence<int, 11>(), std::make_integer_sequence<int, NW>());
         if constexpr (kUnitStride) {
-            uint8_t *op = io.ostage + S * q;
+            // the unit's 64 output bytes, 16-byte aligned in memory when the
+            // buffer is
+            uint8_t *op = io.gout + (int64_t)NB * q;
+            if (((uintptr_t)op & 15) == 0) {
 #pragma unroll
-            for (int c = 0; c < NW / 4; ++c)
-                *reinterpret_cast<uint4 *>(op + 16 * c) = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+                for (int c = 0; c < NW / 4; ++c)
+                    *reinterpret_cast<uint4 *>(op + 16 * c) = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NW; ++i)
+                    for (int j = 0; j < 4; ++j) op[4 * i + j] = (uint8_t)(o[i] >> (8 * j));
+            }
             return;
         }
         o[NW] = 0;

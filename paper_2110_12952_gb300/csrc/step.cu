@@ -64,6 +64,7 @@ struct StepArgs {
     int64_t KL, NT, cells;
     int Px, Py;            // box row pitch and rows per plane (bytes / rows)
     int nring, nbrw, nstage, stage_bytes, tile_bytes;
+    int nhalo;             // padded-unit policies: halo units per tile, sources in `ring`
     int off_bar, off_box, off_tab, off_out, box_bytes;
     int ntab;              // entries of the shared table (cells or groups)
     int KG;                // cells per group (group / quad mode)
@@ -378,7 +379,8 @@ static int rows_preset_of(const fractal *f)
 struct RowsTables {
     int NU = 0, H = 0;
     std::vector<uint32_t> words;   // NU * 4
-    std::vector<uint32_t> ring;
+    std::vector<uint32_t> ring;    // contiguous units: halo cells (ring entries)
+    std::vector<uint32_t> halo;    // padded units: halo unit h's source, tile-table slot << 24 | unit
     bool ok = false;
 };
 
@@ -455,13 +457,19 @@ static RowsTables rows_tables(const fractal *f, int L)
                                  : (v <= -100 ? (uint32_t)(S * (NU + (-100 - v))) : (uint32_t)(S * v));
             t.words[(size_t)q * 4 + d / 2] |= off << (16 * (d % 2));
         }
-    // only the halo bytes some frame cell reads are staged
-    for (int hs = 0; hs < t.H; ++hs)
-        for (int b = 0; b < NB; ++b) {
-            if (!((bytes_read[hs] >> b) & 1u)) continue;
-            t.ring.push_back((uint32_t)(S * (NU + hs) + b) | ((uint32_t)slots[hs].first << 24));
-            t.ring.push_back((uint32_t)(NB * slots[hs].second + b));
+    // padded units: halo units are copied whole; else only the halo bytes
+    // some frame cell reads are staged
+    for (int hs = 0; hs < t.H; ++hs) {
+        if constexpr (S != NB) {
+            t.halo.push_back((uint32_t)slots[hs].second | ((uint32_t)slots[hs].first << 24));
+        } else {
+            for (int b = 0; b < NB; ++b) {
+                if (!((bytes_read[hs] >> b) & 1u)) continue;
+                t.ring.push_back((uint32_t)(S * (NU + hs) + b) | ((uint32_t)slots[hs].first << 24));
+                t.ring.push_back((uint32_t)(NB * slots[hs].second + b));
+            }
         }
+    }
     t.ok = true;
     return t;
 }
@@ -576,7 +584,7 @@ static Layout plan_layout(const fractal *f, int L)
     y.off_tab = off;
     off += round16(4 * g.tab_entries);
     y.off_out = off;
-    off += kStagePad + y.tile_bytes;
+    off += (g.data_bytes > 0) ? 0 : kStagePad + y.tile_bytes;   // padded units store straight to memory
     y.total = off;
     return y;
 }
@@ -722,7 +730,8 @@ int ensure_step_plan(fractal *f)
         p.tapz = t.NU + t.H;
         p.nq = t.NU;
         tab = t.words;
-        ring = t.ring;
+        ring = t.halo.empty() ? t.ring : t.halo;
+        p.nhalo = (int)t.halo.size();
     } else {
         // local lambda -> padded box offset; occupancy of the interior
         std::vector<uint32_t> pos(p.KL);
@@ -831,7 +840,7 @@ int ensure_step_plan(fractal *f)
                 }
 
     }
-    p.nring = (int)(ring.size() / 2);
+    p.nring = p.nhalo ? 0 : (int)(ring.size() / 2);
     FR_CUDA(cudaMalloc(&p.pos, tab.size() * sizeof(uint32_t)));
     FR_CUDA(cudaMemcpy(p.pos, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     if (!ring.empty()) {
@@ -964,6 +973,7 @@ __device__ __forceinline__ void group_from_window(const StepArgs &a, const Rule 
 struct TileIO {
     const uint8_t *data;   // 16-byte aligned stage data; tile cell l at data[a_in + l]
     uint8_t *ostage;       // 16-byte aligned output stage; tile cell l at ostage[a_out + l]
+    uint8_t *gout;         // the tile's first output cell in memory
     int a_in, a_out;
     Rule rule;             // the rule of the tile's instance
 };
@@ -1475,6 +1485,7 @@ __device__ __forceinline__ TileIO tile_io(const StepArgs &a, const TileRef &t, u
     io.ostage = ostage;
     io.a_in = (int)(start & 15);
     io.a_out = (int)(ostart & 15);
+    io.gout = t.out + t.T * a.KL;
     return io;
 }
 
@@ -1496,21 +1507,48 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
         const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
         uint8_t *data = stage + row_bytes + kStagePad;
         const uint8_t *src = t.in + t.T * a.KL;
+        const int32_t *nrow = t.nbr + t.T * a.nbrw;
         const bool al = ((uintptr_t)src & 15) == 0;
+        // halo units (whole units of the neighbouring tiles) after the tile's
+        // units; those of absent tiles are zeros
+        uint32_t copied = 0;
+        for (int h = lane; h < a.nhalo; h += 32) {
+            const uint32_t hw = __ldg(a.ring + h);
+            const int32_t tn = __ldg(nrow + (hw >> 24));
+            uint8_t *dst = data + S * (a.nq + h);
+            if (tn < 0) {
+#pragma unroll
+                for (int c = 0; c < NB / 16; ++c) *reinterpret_cast<uint4 *>(dst + 16 * c) = make_uint4(0, 0, 0, 0);
+            } else if (!al) {
+                const uint8_t *hs = t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu);
+                for (int b = 0; b < NB; ++b) dst[b] = hs[b];
+            } else {
+                copied += NB;
+            }
+        }
         if (!al) {
             for (int u = lane; u < a.nq; u += 32)
                 for (int b = 0; b < NB; ++b) data[S * u + b] = src[NB * u + b];
-            __threadfence_block();
         }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) copied += __shfl_xor_sync(0xffffffffu, copied, o);
+        __threadfence_block();
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-            mbar_arrive_expect_tx(bar, row_bytes + (al ? (uint32_t)(a.nq * NB) : 0u));
-            bulk_g2s(stage, t.nbr + t.T * a.nbrw, row_bytes, bar);
+            mbar_arrive_expect_tx(bar, row_bytes + (al ? (uint32_t)(a.nq * NB) + copied : 0u));
+            bulk_g2s(stage, nrow, row_bytes, bar);
         }
         __syncwarp();
-        if (al)
+        if (al) {
             for (int u = lane; u < a.nq; u += 32) bulk_g2s(data + S * u, src + NB * u, NB, bar);
+            for (int h = lane; h < a.nhalo; h += 32) {
+                const uint32_t hw = __ldg(a.ring + h);
+                const int32_t tn = __ldg(nrow + (hw >> 24));
+                if (tn >= 0)
+                    bulk_g2s(data + S * (a.nq + h), t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu), NB, bar);
+            }
+        }
     }
 }
 
@@ -1527,8 +1565,8 @@ __device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, 
     const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
     const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
     uint8_t *tin = stage + 4 * a.nbrw + kStagePad + (Pol::kUnitStride ? 0 : (int)(start & 15));
-    if (filler && Pol::kUnitStride) {
-        Pol::fill(a, tin, lane);
+    if (Pol::kUnitStride) {
+        return;   // the whole stage arrives by copies (issue_stage)
     } else if (filler) {
         // the bulk copy covered [cf, ct)
         const uintptr_t end = start + (uintptr_t)a.KL;
@@ -1624,24 +1662,16 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         }
         TileIO io = tile_io(a, t, stage, ostage);
         tile_rule<MULTI>(a, Tg, io.rule);
-        if (Pol::kUnitStride || lane == 0) bulk_wait_read_all();   // the previous store has read its bytes
+        if constexpr (Pol::kUnitStride) {
+            // padded units: each thread writes its unit straight to memory
+            Pol::compute(a, io, nullptr, tab, R);
+        } else {
+        if (lane == 0) bulk_wait_read_all();   // this warp's previous store has read its bytes
         __syncwarp();
         Pol::compute(a, io, nullptr, tab, R);
         fence_proxy_async_smem();             // this thread's writes, before the bulk copy reads them
         __syncwarp();
-        if constexpr (Pol::kUnitStride) {
-            // each thread stores its own unit
-            if (tid < a.nq) {
-                uint8_t *dst = t.out + t.T * a.KL + (int64_t)Pol::NB * tid;
-                const uint8_t *so = ostage + Pol::kUnitStride * tid;
-                if (((uintptr_t)dst & 15) == 0) {
-                    bulk_s2g(dst, so, Pol::NB);
-                    bulk_commit();
-                } else {
-                    for (int b = 0; b < Pol::NB; ++b) dst[b] = so[b];
-                }
-            }
-        } else if (wb1 > wb0) {
+        if (wb1 > wb0) {
             // ostage[al + j] holds tile byte j; the warp's bytes [wb0, wb1)
             // are a bulk copy between their first and last 16-byte
             // boundaries in memory and plain stores around them
@@ -1659,6 +1689,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
             } else {
                 for (int j = wb0 + lane; j < wb1; j += 32) ob[j] = ostage[al + j];
             }
+        }
         }
         ok = true;
         if (has_next) {
@@ -1681,7 +1712,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         sn = (sn + 1 == a.nstage) ? 0 : sn + 1;
         if (sn == 0) pn ^= 1u;
     }
-    if (Pol::kUnitStride || lane == 0) bulk_wait_all();
+    if (!Pol::kUnitStride && lane == 0) bulk_wait_all();
 }
 
 // Tile loop of the policies that compute from the box: wait for the tile's
@@ -1849,6 +1880,12 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         fence_proxy_async_smem();
     }
     if constexpr (Pol::kRingInTile) {
+        if constexpr (Pol::kUnitStride) {
+            // the all-zero unit of every stage (no copy ever writes it)
+            for (int s = 0; s < a.nstage; ++s)
+                for (int j = tid; j < Pol::NB; j += nth)
+                    smem[s * a.stage_bytes + 4 * a.nbrw + kStagePad + Pol::kUnitStride * a.tapz + j] = 0;
+        }
         if (tid < 32) {
             __syncwarp();
             for (int s = 0; s < a.nstage; ++s) {
@@ -1918,6 +1955,7 @@ static void fill_args(const fractal *f, StepArgs &a)
     a.Px = p.Px;
     a.Py = p.Py;
     a.nring = p.nring;
+    a.nhalo = p.nhalo;
     a.nbrw = p.nbrw;
     a.nstage = p.nstage;
     a.stage_bytes = p.stage_bytes;
