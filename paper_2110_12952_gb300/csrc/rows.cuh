@@ -232,6 +232,7 @@ struct RowsPolicy {
     // bytes between units in the stages (0: the tile's bytes as one copy)
     static constexpr int kUnitStride = rp_stride<P>() == NB ? 0 : rp_stride<P>();
     static constexpr int S = rp_stride<P>();
+    static constexpr bool kRingByAll = true;    // hundreds of halo cells per tile: every thread helps
     // bytes of the last word that belong to the unit
     static constexpr uint32_t kLastMask = (NB % 4) ? (0xffffffffu >> (8 * (4 - NB % 4))) : 0xffffffffu;
     struct Regs {

@@ -1282,6 +1282,7 @@ __device__ __forceinline__ void ext_taps(const uint8_t *tin, const uint32_t *e, 
 struct TapPolicy {
     static constexpr bool kRingInTile = true;   // halo bytes go after the tile's bytes
     static constexpr int kUnitStride = 0;       // the tile's bytes as one copy
+    static constexpr bool kRingByAll = false;   // 8 halo cells per tile: one warp fills them
     static constexpr int NW = (kUnitCells + 3) / 4;   // 21 words per unit
     struct Regs {
         uint32_t e[kExtGroups];   // byte offsets 9 g of the unit's external groups
@@ -1581,24 +1582,37 @@ __device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, 
         }
         Pol::fill(a, tin, lane);
     }
-#pragma unroll
-    for (int k = 0; k < kRingRegs; ++k) {
-        const int e = tid + k * nth;
-        if (e < a.nring) {
+    if constexpr (!Pol::kRingByAll) {
+        // a short ring: the filling warp alone, entry `lane` prefetched
+        for (int e = filler ? lane : a.nring; e < a.nring; e += 32) {
             const uint32_t w0 = __ldg(a.ring + 2 * e);
-            uint32_t v = rv[k];
-            if (!pref) {
+            uint32_t v = rv[0];
+            if (!pref || e != lane) {
                 const int32_t tn = nrow[w0 >> 24];
                 v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
             }
             tin[w0 & 0xffffff] = v != 0;
         }
-    }
-    for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
-        const uint32_t w0 = __ldg(a.ring + 2 * e);
-        const int32_t tn = nrow[w0 >> 24];
-        const uint32_t v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
-        tin[w0 & 0xffffff] = v != 0;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRingRegs; ++k) {
+            const int e = tid + k * nth;
+            if (e < a.nring) {
+                const uint32_t w0 = __ldg(a.ring + 2 * e);
+                uint32_t v = rv[k];
+                if (!pref) {
+                    const int32_t tn = nrow[w0 >> 24];
+                    v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+                }
+                tin[w0 & 0xffffff] = v != 0;
+            }
+        }
+        for (int e = tid + kRingRegs * nth; e < a.nring; e += nth) {
+            const uint32_t w0 = __ldg(a.ring + 2 * e);
+            const int32_t tn = nrow[w0 >> 24];
+            const uint32_t v = (tn >= 0) ? t.in[(int64_t)tn * a.KL + __ldg(a.ring + 2 * e + 1)] : 0u;
+            tin[w0 & 0xffffff] = v != 0;
+        }
     }
 }
 
@@ -1647,7 +1661,14 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         // the next tile's halo values, when its stage has landed already
         // (never waited for here): the loads stay in flight during the compute
         bool pref = false;
-        if (has_next && tid < a.nring && mbar_test(&bars[sn], pn)) {
+        if constexpr (!Pol::kRingByAll) {
+            if (filler && has_next && lane < a.nring && mbar_test(&bars[sn], pn)) {
+                const uint32_t w0 = __ldg(a.ring + 2 * lane);
+                const int32_t tnb = reinterpret_cast<const int32_t *>(next_stage)[w0 >> 24];
+                rv[0] = (tnb >= 0) ? tn.in[(int64_t)tnb * a.KL + __ldg(a.ring + 2 * lane + 1)] : 0u;
+                pref = true;
+            }
+        } else if (has_next && tid < a.nring && mbar_test(&bars[sn], pn)) {
             const int32_t *nrow_n = reinterpret_cast<const int32_t *>(next_stage);
 #pragma unroll
             for (int k = 0; k < kRingRegs; ++k) {
