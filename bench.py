@@ -41,7 +41,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_traffic.json")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--r", type=int, default=20, help="triangle level of the headline workload")
@@ -110,7 +110,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -120,7 +120,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def wait_ready(self, timeout=5.0):
+        """Wait for the first sample (nvidia-smi takes a moment to start)."""
+        t_end = time.monotonic() + timeout
+        while self.proc is not None and not self.lines and time.monotonic() < t_end:
+            time.sleep(0.01)
+
+    def window(self, t0, t1):
+        """Keep only the samples taken between t0 and t1 (monotonic clock)."""
+        self.lines = [(t, l) for t, l in self.lines if t0 <= t <= t1]
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -133,7 +143,7 @@ class ClockSampler:
 
     def summary(self):
         rows = []
-        for l in self.lines:
+        for _, l in self.lines:
             p = [x.strip() for x in l.split(",")]
             if len(p) < 9:
                 continue
@@ -268,22 +278,28 @@ def run_ours(args, rank, world, dist):
         g.step(bufs[cur[0]], out=bufs[1 - cur[0]], steps=1)
         cur[0] ^= 1
 
-    # warm-up, then exactly K timed generations bracketed by barrier + sync
-    for _ in range(args.warmup):
-        one_generation()
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # warm-up, then exactly K timed generations bracketed by barrier + sync;
+    # the clock sampler starts before the warm-up and keeps only the samples
+    # taken inside the timed region
     with ClockSampler(dev.index) as clocks:
+        for _ in range(args.warmup):
+            one_generation()
+        torch.cuda.synchronize()
+        clocks.wait_ready()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        t_start = time.monotonic()
         ev0.record(stream)
         for _ in range(args.steps):
             one_generation()
         ev1.record(stream)
         torch.cuda.synchronize()
+        t_end = time.monotonic()
+    clocks.window(t_start, t_end)
     if dist is not None:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
