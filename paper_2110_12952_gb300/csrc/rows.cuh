@@ -222,6 +222,59 @@ __device__ __forceinline__ void unit_band(const uint8_t *tin, const uint32_t *e,
     (band_word<P, Y, I>(rule, v, t, o), ...);
 }
 
+// Bytes 0..NB-1 of unit q (NB bytes per unit, contiguous in the stage) as
+// words v[0..NW-1], cells 0 or 1 (bytes past the unit: whatever follows).
+template <int NB, int NW>
+__device__ __forceinline__ void load_unit(const TileIO &io, int q, uint32_t *v)
+{
+    constexpr uint32_t kLastMask = (NB % 4) ? (0xffffffffu >> (8 * (4 - NB % 4))) : 0xffffffffu;
+    const int off = io.a_in + NB * q;
+    const uint8_t *wp = io.data + (off & ~3);
+    const uint32_t sh = (uint32_t)(off & 3) * 8u;
+    uint32_t w[NW + 1];
+#pragma unroll
+    for (int i = 0; i <= NW; ++i) w[i] = lds32(wp + 4 * i);
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        v[i] = __funnelshift_r(w[i], w[i + 1], sh);
+        any |= (i == NW - 1) ? (v[i] & kLastMask) : v[i];
+    }
+    if (any & 0xfefefefeu) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) v[i] = bytes_to_01(v[i]);
+    }
+}
+
+// Bytes 0..NB-1 of o to unit q of the output stage: word i of the aligned run
+// from the unit's first byte - m holds bytes 4i - m .. 4i - m + 3; words
+// holding only this unit's bytes are stored whole, the others byte by byte.
+// o has NW + 1 words, o[NW] = 0.
+template <int NB, int NW>
+__device__ __forceinline__ void store_unit(const TileIO &io, int q, const uint32_t *o)
+{
+    uint8_t *ob = io.ostage + io.a_out + NB * q;
+    const uint32_t m = (uint32_t)(io.a_out + NB * q) & 3u;
+    uint8_t *base = ob - m;
+    const uint32_t sl = 8u * m;
+#pragma unroll
+    for (int i = 0; i <= NW; ++i) {
+        const uint32_t wv = (i == 0) ? (o[0] << sl) : __funnelshift_l(o[i - 1], o[i], sl);
+        if (4 * i >= 3 && 4 * i + 4 <= NB) {
+            sts32(base + 4 * i, wv);
+        } else {
+            const int lo = 4 * i - (int)m;   // byte of the unit at the word's byte 0
+            if (lo >= 0 && lo + 4 <= NB) {
+                sts32(base + 4 * i, wv);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (lo + j >= 0 && lo + j < NB) base[4 * i + j] = (uint8_t)(wv >> (8 * j));
+            }
+        }
+    }
+}
+
 template <int P>
 struct RowsPolicy {
     static constexpr bool kRingInTile = true;   // halo units go after the tile's bytes
@@ -233,8 +286,6 @@ struct RowsPolicy {
     static constexpr int kUnitStride = rp_stride<P>() == NB ? 0 : rp_stride<P>();
     static constexpr int S = rp_stride<P>();
     static constexpr bool kRingByAll = true;    // hundreds of halo cells per tile: every thread helps
-    // bytes of the last word that belong to the unit
-    static constexpr uint32_t kLastMask = (NB % 4) ? (0xffffffffu >> (8 * (4 - NB % 4))) : 0xffffffffu;
     struct Regs {
         uint32_t e[8];   // byte offsets of the 8 neighbouring units (W..E, N..S)
     };
@@ -281,22 +332,12 @@ struct RowsPolicy {
             }
 #pragma unroll
             for (int i = 0; i < NW; ++i) any |= v[i];
-        } else {
-            const int off = io.a_in + NB * q;
-            const uint8_t *wp = io.data + (off & ~3);
-            const uint32_t sh = (uint32_t)(off & 3) * 8u;
-            uint32_t w[NW + 1];
+            if (any & 0xfefefefeu) {
 #pragma unroll
-            for (int i = 0; i <= NW; ++i) w[i] = lds32(wp + 4 * i);
-#pragma unroll
-            for (int i = 0; i < NW; ++i) {
-                v[i] = __funnelshift_r(w[i], w[i + 1], sh);
-                any |= (i == NW - 1) ? (v[i] & kLastMask) : v[i];
+                for (int i = 0; i < NW; ++i) v[i] = bytes_to_01(v[i]);
             }
-        }
-        if (any & 0xfefefefeu) {
-#pragma unroll
-            for (int i = 0; i < NW; ++i) v[i] = bytes_to_01(v[i]);
+        } else {
+            load_unit<NB, NW>(io, q, v);
         }
         const uint8_t *tin = kUnitStride ? io.data : io.data + io.a_in;
         uint32_t x[NE], r[33], t[27], o[NW + 1];
@@ -322,29 +363,7 @@ struct RowsPolicy {
             return;
         }
         o[NW] = 0;
-        // bytes 0..NB-1 of o at ob: word i of the aligned run from ob - m
-        // holds bytes 4i - m .. 4i - m + 3; words holding only this unit's
-        // bytes are stored whole, the others byte by byte
-        uint8_t *ob = io.ostage + io.a_out + NB * q;
-        const uint32_t m = (uint32_t)(io.a_out + NB * q) & 3u;
-        uint8_t *base = ob - m;
-        const uint32_t sl = 8u * m;
-#pragma unroll
-        for (int i = 0; i <= NW; ++i) {
-            const uint32_t wv = (i == 0) ? (o[0] << sl) : __funnelshift_l(o[i - 1], o[i], sl);
-            if (4 * i >= 3 && 4 * i + 4 <= NB) {
-                sts32(base + 4 * i, wv);
-            } else {
-                const int lo = 4 * i - (int)m;   // stream byte of the word's byte 0
-                if (lo >= 0 && lo + 4 <= NB) {
-                    sts32(base + 4 * i, wv);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (lo + j >= 0 && lo + j < NB) base[4 * i + j] = (uint8_t)(wv >> (8 * j));
-                }
-            }
-        }
+        store_unit<NB, NW>(io, q, o);
     }
 };
 

@@ -53,6 +53,7 @@
 #include "step.h"
 #include "tma.cuh"
 #include "rows_layout.h"
+#include "lid_layout.h"
 
 namespace fr {
 
@@ -141,7 +142,7 @@ static int group_levels(const fractal *f)
     return 0;
 }
 
-enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10, kModeRows0 = 11, kModeRows1 = 12 };
+enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10, kModeRows0 = 11, kModeRows1 = 12, kModeLid1 = 13 };
 
 // ---- tap mode: the Sierpinski triangle with offsets (0,0), (1,0), (0,1)
 // A level-2 group is 9 cells (lid 0..8 at kPosX/kPosY) filling a 4x4 block.
@@ -474,6 +475,96 @@ static RowsTables rows_tables(const fractal *f, int L)
     return t;
 }
 
+// ---- lid mode: the Vicsek fractal in level-3 units (see lid_layout.h)
+constexpr int kLidPreset = 1, kLidLevels = 3;
+
+// Tables of lid mode for tile depth L (>= kLidLevels), laid out as those of
+// rows mode with units of k^3 cells (27x27 blocks).
+template <int P, int U>
+static RowsTables lid_tables(const fractal *f, int L)
+{
+    RowsTables t;
+    constexpr int NB = LidUnit<P, U>::NB, SIDE = LidUnit<P, U>::side, NE = lu_next<P, U>();
+    if (rows_preset_of(f) != P || L < U) return t;
+    int side = 1, NU = 1;
+    for (int i = 0; i < L - U; ++i) {
+        side *= 3;
+        NU *= RowsPreset<P>::k;
+    }
+    t.NU = NU;
+    std::vector<int> M((size_t)side * side, -1);
+    std::vector<int> ux(NU), uy(NU);
+    for (int q = 0; q < NU; ++q) {
+        int c[3];
+        host_lambda(f, q, L - U, c);
+        ux[q] = c[0];
+        uy[q] = c[1];
+        M[(size_t)c[1] * side + c[0]] = q;
+    }
+    // the unit layout against the fractal's own lambda
+    for (int q = 0; q < NU; ++q)
+        for (int u = 0; u < NB; ++u) {
+            int c[3];
+            host_lambda(f, (int64_t)NB * q + u, L, c);
+            if (c[0] != SIDE * ux[q] + lu_x<P, U>(u) || c[1] != SIDE * uy[q] + lu_y<P, U>(u)) return t;
+        }
+    std::vector<std::vector<int>> dir_bytes(8);   // per direction: the unit bytes the frame reads
+    for (int e = 0; e < NE; ++e) {
+        const int x = lu_ext_x<P, U>(e), y = lu_ext_y<P, U>(e);
+        dir_bytes[lu_dir<P, U>(x, y)].push_back(lu_fbyte<P, U>(x, y));
+    }
+    std::map<std::pair<int, int>, int> slot_of;   // (tile-table slot, unit there) -> halo unit
+    std::vector<std::pair<int, int>> slots;
+    std::vector<std::vector<uint8_t>> bytes_read;
+    std::vector<int> nb((size_t)NU * 8);
+    for (int q = 0; q < NU; ++q)
+        for (int d = 0; d < 8; ++d) {
+            const int d9 = d < 4 ? d : d + 1;
+            int nx = ux[q] + d9 % 3 - 1, ny = uy[q] + d9 / 3 - 1;
+            const int tdx = nx < 0 ? -1 : (nx >= side ? 1 : 0), tdy = ny < 0 ? -1 : (ny >= side ? 1 : 0);
+            nx = (nx + side) % side;
+            ny = (ny + side) % side;
+            const int gn = M[(size_t)ny * side + nx];
+            int v = -2;   // -2: the zero unit
+            if (gn >= 0 && !dir_bytes[d].empty()) {
+                if (tdx == 0 && tdy == 0) v = gn;
+                else {
+                    const int t9 = (tdx + 1) + 3 * (tdy + 1);
+                    const int tslot = t9 < 4 ? t9 : t9 - 1;
+                    auto key = std::make_pair(tslot, gn);
+                    auto it = slot_of.find(key);
+                    if (it == slot_of.end()) {
+                        it = slot_of.emplace(key, (int)slots.size()).first;
+                        slots.push_back(key);
+                        bytes_read.emplace_back(NB, 0);
+                    }
+                    for (int b : dir_bytes[d]) bytes_read[it->second][b] = 1;
+                    v = -100 - it->second;
+                }
+            }
+            nb[(size_t)q * 8 + d] = v;
+        }
+    t.H = (int)slots.size();
+    const int64_t zero = NU + t.H;
+    if ((int64_t)NB * zero + NB >= 65536) return t;
+    t.words.assign((size_t)NU * 4, 0);
+    for (int q = 0; q < NU; ++q)
+        for (int d = 0; d < 8; ++d) {
+            const int v = nb[(size_t)q * 8 + d];
+            const uint32_t off = (v == -2) ? (uint32_t)(NB * zero)
+                                 : (v <= -100 ? (uint32_t)(NB * (NU + (-100 - v))) : (uint32_t)(NB * v));
+            t.words[(size_t)q * 4 + d / 2] |= off << (16 * (d % 2));
+        }
+    for (int hs = 0; hs < t.H; ++hs)
+        for (int b = 0; b < NB; ++b) {
+            if (!bytes_read[hs][b]) continue;
+            t.ring.push_back((uint32_t)(NB * (NU + hs) + b) | ((uint32_t)slots[hs].first << 24));
+            t.ring.push_back((uint32_t)(NB * slots[hs].second + b));
+        }
+    t.ok = true;
+    return t;
+}
+
 struct Geometry {
     int mode, G, xoff, halo;
     int64_t B, Px, Py, planes;
@@ -514,6 +605,19 @@ static Geometry plan_geometry(const fractal *f, int L)
         }
     }
     const int rp = rows_preset_of(f);
+    if (rp == kLidPreset && L >= kLidLevels && ipow(f->k, L - kLidLevels) <= 256) {
+        const RowsTables t = lid_tables<kLidPreset, kLidLevels>(f, L);
+        if (t.ok) {
+            g.mode = kModeLid1;
+            g.Px = g.Py = g.planes = 0;
+            g.tab_entries = 0;   // the unit tables live in registers
+            g.halo = t.H;
+            g.halo_bytes = (int64_t)ipow(f->k, kLidLevels) * (t.H + 1);
+            g.block = std::max<int64_t>(64, ((int64_t)t.NU + 31) / 32 * 32);
+            g.box_bytes = 0;
+            return g;
+        }
+    }
     if (rp >= 0 && L >= 2 && ipow(f->k, L - 2) <= 256) {
         const RowsTables t = rp == 0 ? rows_tables<0>(f, L) : rows_tables<1>(f, L);
         if (t.ok) {
@@ -569,7 +673,8 @@ static Layout plan_layout(const fractal *f, int L)
     Layout y;
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
-    y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1) ? 2 : nstages();
+    y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1 ||
+                g.mode == kModeLid1) ? 2 : nstages();
     // slack: 16-byte rounding of the bulk copy, whole-word reads and writes
     // past the tile's last cell; tap mode: halo and zero groups
     y.tile_bytes = round16((g.data_bytes > 0 ? g.data_bytes : KL + g.halo_bytes) + 64);
@@ -724,6 +829,13 @@ int ensure_step_plan(fractal *f)
         p.nq = t.NQ;
         tab = t.words;
         ring = t.ring;
+    } else if (p.mode == kModeLid1) {
+        const RowsTables t = lid_tables<kLidPreset, kLidLevels>(f, L);
+        p.KG = (int)ipow(f->k, kLidLevels);
+        p.tapz = t.NU + t.H;
+        p.nq = t.NU;
+        tab = t.words;
+        ring = t.ring;
     } else if (p.mode == kModeRows0 || p.mode == kModeRows1) {
         const RowsTables t = p.mode == kModeRows0 ? rows_tables<0>(f, L) : rows_tables<1>(f, L);
         p.KG = f->k * f->k;
@@ -865,6 +977,7 @@ int ensure_step_plan(fractal *f)
     else if (p.mode == kModeTap) rc = configure<2, kModeTap>(p, f->num_sms);
     else if (p.mode == kModeRows0) rc = configure<2, kModeRows0>(p, f->num_sms);
     else if (p.mode == kModeRows1) rc = configure<2, kModeRows1>(p, f->num_sms);
+    else if (p.mode == kModeLid1) rc = configure<2, kModeLid1>(p, f->num_sms);
     else if (p.mode == kModeGroup4) rc = configure<2, kModeGroup4>(p, f->num_sms);
     else if (p.mode == kModeGroup3) rc = configure<2, kModeGroup3>(p, f->num_sms);
     else rc = configure<2, kModeCell>(p, f->num_sms);
@@ -1382,6 +1495,7 @@ struct TapPolicy {
 
 }  // namespace fr
 #include "rows.cuh"
+#include "lid.cuh"
 namespace fr {
 
 template <int DIM, int MODE>
@@ -1400,6 +1514,8 @@ template <>
 struct PolicyOf<2, kModeRows0> { using type = RowsPolicy<0>; };
 template <>
 struct PolicyOf<2, kModeRows1> { using type = RowsPolicy<1>; };
+template <>
+struct PolicyOf<2, kModeLid1> { using type = LidPolicy<kLidPreset, kLidLevels>; };
 
 // A tile of the launch resolved to its instance's buffers, table and rule.
 struct TileRef {
@@ -1885,7 +2001,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
 }
 
 template <int DIM, int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, MODE == kModeTap || MODE == kModeRows0 || MODE == kModeRows1 ? 3 : 4)
+__global__ void __launch_bounds__(256, MODE == kModeTap || MODE == kModeRows0 || MODE == kModeRows1 || MODE == kModeLid1 ? 3 : 4)
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     using Pol = typename PolicyOf<DIM, MODE>::type;
@@ -2020,6 +2136,8 @@ static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t
         step_tma_kernel<2, kModeRows0, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeRows1)
         step_tma_kernel<2, kModeRows1, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (p.mode == kModeLid1)
+        step_tma_kernel<2, kModeLid1, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup4)
         step_tma_kernel<2, kModeGroup4, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeGroup3)

@@ -170,8 +170,9 @@ def test_nonbinary_input_every_depth(P, fam, r, L):
     assert np.array_equal(out.cpu().numpy(), o.step(raw, rule=oracle_rule(fam), steps=1)), f"L={L}"
 
 
-@pytest.mark.parametrize("fam,r,L", [(W.CARPET, 8, L) for L in (2, 3, 4)] + [(W.VICSEK, 9, L) for L in (2, 3, 4, 5)])
-def test_rows_policy_many_tiles_per_cta(P, fam, r, L):
+@pytest.mark.parametrize("fam,r,L", [(W.CARPET, 8, L) for L in (2, 3, 4)] +
+                         [(W.VICSEK, 9, L) for L in (2, 3, 4, 5, 6)] + [(W.VICSEK, 10, 6)])
+def test_rows_and_lid_policies_many_tiles_per_cta(P, fam, r, L):
     # thousands of tiles per launch: every CTA reuses its stages many times
     g, o = gpu_fr(P, fam, r), ora(fam, r)
     init = o.init_bernoulli(9, 0.5)
@@ -367,6 +368,12 @@ def test_plan_info(P):
     assert ci["policy_name"] == "rows_carpet" and ci["block"] == 64   # 8^2 units of 64 cells
     c.tile_levels = 1
     assert c.plan_info()["policy_name"] in ("group3", "cell")
+    v = gpu_fr(P, W.VICSEK, 8)
+    v.tile_levels = 6
+    vi = v.plan_info()
+    assert vi["policy_name"] == "lid_vicsek" and vi["block"] == 128   # 5^3 units of 125 cells
+    v.tile_levels = 2
+    assert v.plan_info()["policy_name"] == "rows_vicsek"
     arr = (ctypes.c_int32 * 8)()
     assert g._lib.fractal_plan_info(g._h, arr, 0) != 0
     assert g._lib.fractal_plan_info(g._h, arr, 8) != 0
