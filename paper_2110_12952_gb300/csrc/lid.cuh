@@ -70,7 +70,8 @@ __device__ __forceinline__ void lid_exts(const uint8_t *tin, const uint32_t *e, 
 template <int P, int U>
 struct LidPolicy {
     static constexpr bool kRingInTile = true;    // halo units go after the tile's bytes
-    static constexpr int kUnitStride = 0;        // the tile's bytes as one copy
+    static constexpr bool kPadded = false;       // the tile's bytes as one copy
+    __host__ __device__ static constexpr int slot(int n) { return LidUnit<P, U>::NB * n; }
     static constexpr bool kRingByAll = false;    // a few halo cells per tile
     static constexpr int NB = LidUnit<P, U>::NB;
     static constexpr int NW = (NB + 3) / 4;

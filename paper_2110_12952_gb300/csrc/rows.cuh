@@ -282,14 +282,15 @@ struct RowsPolicy {
     static constexpr int NB = K * K;            // bytes per unit
     static constexpr int NW = (NB + 3) / 4;     // words per unit
     static constexpr int NE = rp_next<P>();     // external cells per unit
-    // bytes between units in the stages (0: the tile's bytes as one copy)
-    static constexpr int kUnitStride = rp_stride<P>() == NB ? 0 : rp_stride<P>();
-    static constexpr int S = rp_stride<P>();
+    // units in their own slots of the stages (rp_slot), else the tile's
+    // bytes as one copy
+    static constexpr bool kPadded = rp_padded<P>();
+    __host__ __device__ static constexpr int slot(int n) { return rp_slot<P>(n); }
     static constexpr bool kRingByAll = true;    // hundreds of halo cells per tile: every thread helps
     struct Regs {
         uint32_t e[8];   // byte offsets of the 8 neighbouring units (W..E, N..S)
     };
-    static_assert(kUnitStride == 0 || (NB % 16 == 0 && kUnitStride % 16 == 0), "padded units move in 16-byte pieces");
+    static_assert(!kPadded || NB == 64, "padded units are 64-byte pairs");
     __device__ static void init(const StepArgs &a, Regs &R)
     {
         const int q = threadIdx.x;
@@ -303,7 +304,7 @@ struct RowsPolicy {
     // the all-zero unit, after the halo units, by the lanes of the filling warp
     __device__ static void fill(const StepArgs &a, uint8_t *tin, int lane)
     {
-        for (int j = lane; j < NB; j += 32) tin[S * a.tapz + j] = 0;
+        for (int j = lane; j < NB; j += 32) tin[slot(a.tapz) + j] = 0;
     }
     __device__ static void warp_bytes(const StepArgs &a, int w, int *b0, int *b1)
     {
@@ -319,9 +320,9 @@ struct RowsPolicy {
         if (q >= a.nq) return;
         uint32_t v[NW];
         uint32_t any = 0;
-        if constexpr (kUnitStride) {
+        if constexpr (kPadded) {
             // the unit sits 16-byte aligned at its own slot
-            const uint8_t *up = io.data + S * q;
+            const uint8_t *up = io.data + slot(q);
 #pragma unroll
             for (int c = 0; c < NW / 4; ++c) {
                 const uint4 w4 = *reinterpret_cast<const uint4 *>(up + 16 * c);
@@ -339,7 +340,7 @@ struct RowsPolicy {
         } else {
             load_unit<NB, NW>(io, q, v);
         }
-        const uint8_t *tin = kUnitStride ? io.data : io.data + io.a_in;
+        const uint8_t *tin = kPadded ? io.data : io.data + io.a_in;
         uint32_t x[NE], r[33], t[27], o[NW + 1];
         unit_band<P, 0>(tin, R.e, io.rule, v, x, r, t, o, std::make_integer_sequence<int, NE>(),
                         std::make_integer_sequence<int, 11>(), std::make_integer_sequence<int, NW>());
@@ -347,7 +348,7 @@ struct RowsPolicy {
                         std::make_integer_sequence<int, 11>(), std::make_integer_sequence<int, NW>());
         unit_band<P, 2>(tin, R.e, io.rule, v, x, r, t, o, std::make_integer_sequence<int, NE>(),
                         std::make_integer_sequence<int, 11>(), std::make_integer_sequence<int, NW>());
-        if constexpr (kUnitStride) {
+        if constexpr (kPadded) {
             // the unit's 64 output bytes, 16-byte aligned in memory when the
             // buffer is
             uint8_t *op = io.gout + (int64_t)NB * q;

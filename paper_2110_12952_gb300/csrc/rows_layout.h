@@ -54,15 +54,20 @@ constexpr int rp_byte(int x, int y)
     return (j < 0 || l < 0) ? -1 : RowsPreset<P>::k * j + l;
 }
 
-// Bytes between consecutive units in a stage: the carpet's 64-byte units sit
-// 80 bytes apart (16-byte loads and stores of 8 consecutive units then hit 8
-// different bank groups; at 64 bytes every unit would start in one of 2
-// banks), each copied in and out on its own; the Vicsek fractal's 25-byte
-// units stay contiguous.
+// Byte offset of unit slot n in a stage.  The carpet's 64-byte units sit in
+// pairs with a 16-byte gap after each pair: 16-byte loads of 8 consecutive
+// units then hit 8 different bank groups (at a plain 64-byte stride every
+// unit would start in one of 2 banks), and one bulk copy brings two units.
+// The Vicsek fractal's 25-byte units stay contiguous.
 template <int P>
-constexpr int rp_stride()
+constexpr bool rp_padded()
 {
-    return P == 0 ? 80 : RowsPreset<P>::k * RowsPreset<P>::k;
+    return P == 0;
+}
+template <int P>
+constexpr int rp_slot(int n)
+{
+    return rp_padded<P>() ? 144 * (n >> 1) + 64 * (n & 1) : RowsPreset<P>::k * RowsPreset<P>::k * n;
 }
 
 template <int P>

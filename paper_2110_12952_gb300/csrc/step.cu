@@ -374,9 +374,10 @@ static int rows_preset_of(const fractal *f)
 // Tables of rows mode for tile depth L (>= 2): per unit (level-2 subtree of
 // the tile), the byte offsets (uint16, two per word) of its 8 neighbouring
 // units in the order of frame_dir, from the tile's first cell in the stage:
-// units of the tile at S u (S = rp_stride), halo units of neighbouring tiles
-// at S (NU + h), an all-zero unit after them; and the halo bytes to fetch per
-// tile (ring entries as in tap mode).
+// units of the tile at slot u (rp_slot), halo units of neighbouring tiles at
+// slot NU + h, an all-zero unit after them; and the halo bytes to fetch per
+// tile (ring entries as in tap mode), or for padded units the halo units to
+// copy whole.
 struct RowsTables {
     int NU = 0, H = 0;
     std::vector<uint32_t> words;   // NU * 4
@@ -389,7 +390,7 @@ template <int P>
 static RowsTables rows_tables(const fractal *f, int L)
 {
     RowsTables t;
-    constexpr int K = RowsPreset<P>::k, NB = K * K, S = rp_stride<P>();
+    constexpr int K = RowsPreset<P>::k, NB = K * K;
     if (rows_preset_of(f) != P || L < 2) return t;
     int side = 1, NU = 1;
     for (int i = 0; i < L - 2; ++i) {
@@ -449,24 +450,23 @@ static RowsTables rows_tables(const fractal *f, int L)
         }
     t.H = (int)slots.size();
     const int64_t zero = NU + t.H;
-    if ((int64_t)S * zero + NB >= 65536) return t;
+    if ((int64_t)rp_slot<P>((int)zero) + NB >= 65536) return t;
     t.words.assign((size_t)NU * 4, 0);
     for (int q = 0; q < NU; ++q)
         for (int d = 0; d < 8; ++d) {
             const int v = nb[(size_t)q * 8 + d];
-            const uint32_t off = (v == -2) ? (uint32_t)(S * zero)
-                                 : (v <= -100 ? (uint32_t)(S * (NU + (-100 - v))) : (uint32_t)(S * v));
+            const uint32_t off = (uint32_t)rp_slot<P>(v == -2 ? (int)zero : (v <= -100 ? NU + (-100 - v) : v));
             t.words[(size_t)q * 4 + d / 2] |= off << (16 * (d % 2));
         }
     // padded units: halo units are copied whole; else only the halo bytes
     // some frame cell reads are staged
     for (int hs = 0; hs < t.H; ++hs) {
-        if constexpr (S != NB) {
+        if constexpr (rp_padded<P>()) {
             t.halo.push_back((uint32_t)slots[hs].second | ((uint32_t)slots[hs].first << 24));
         } else {
             for (int b = 0; b < NB; ++b) {
                 if (!((bytes_read[hs] >> b) & 1u)) continue;
-                t.ring.push_back((uint32_t)(S * (NU + hs) + b) | ((uint32_t)slots[hs].first << 24));
+                t.ring.push_back((uint32_t)(rp_slot<P>(NU + hs) + b) | ((uint32_t)slots[hs].first << 24));
                 t.ring.push_back((uint32_t)(NB * slots[hs].second + b));
             }
         }
@@ -626,7 +626,7 @@ static Geometry plan_geometry(const fractal *f, int L)
             g.tab_entries = 0;   // the unit tables live in registers
             g.halo = t.H;
             g.halo_bytes = (int64_t)f->k * f->k * (t.H + 1);
-            g.data_bytes = (rp == 0) ? (int64_t)rp_stride<0>() * (t.NU + t.H + 1) : 0;
+            g.data_bytes = rp_padded<0>() && rp == 0 ? (int64_t)rp_slot<0>(t.NU + t.H + 1) : 0;
             g.block = std::max<int64_t>(64, ((int64_t)t.NU + 31) / 32 * 32);
             g.box_bytes = 0;
             return g;
@@ -1394,7 +1394,7 @@ __device__ __forceinline__ void ext_taps(const uint8_t *tin, const uint32_t *e, 
 
 struct TapPolicy {
     static constexpr bool kRingInTile = true;   // halo bytes go after the tile's bytes
-    static constexpr int kUnitStride = 0;       // the tile's bytes as one copy
+    static constexpr bool kPadded = false;      // the tile's bytes as one copy
     static constexpr bool kRingByAll = false;   // 8 halo cells per tile: one warp fills them
     static constexpr int NW = (kUnitCells + 3) / 4;   // 21 words per unit
     struct Regs {
@@ -1614,13 +1614,13 @@ template <bool MULTI, class Pol>
 __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t, uint8_t *stage, uint64_t *bar)
 {
     const int lane = threadIdx.x & 31;
-    if constexpr (Pol::kUnitStride == 0) {
+    if constexpr (!Pol::kPadded) {
         if (lane == 0) {
             fence_proxy_async_smem();
             issue_tile(a, t, stage, bar);
         }
     } else {
-        constexpr int S = Pol::kUnitStride, NB = Pol::NB;
+        constexpr int NB = Pol::NB;
         const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
         uint8_t *data = stage + row_bytes + kStagePad;
         const uint8_t *src = t.in + t.T * a.KL;
@@ -1632,7 +1632,7 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
         for (int h = lane; h < a.nhalo; h += 32) {
             const uint32_t hw = __ldg(a.ring + h);
             const int32_t tn = __ldg(nrow + (hw >> 24));
-            uint8_t *dst = data + S * (a.nq + h);
+            uint8_t *dst = data + Pol::slot(a.nq + h);
             if (tn < 0) {
 #pragma unroll
                 for (int c = 0; c < NB / 16; ++c) *reinterpret_cast<uint4 *>(dst + 16 * c) = make_uint4(0, 0, 0, 0);
@@ -1645,7 +1645,7 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
         }
         if (!al) {
             for (int u = lane; u < a.nq; u += 32)
-                for (int b = 0; b < NB; ++b) data[S * u + b] = src[NB * u + b];
+                for (int b = 0; b < NB; ++b) data[Pol::slot(u) + b] = src[NB * u + b];
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) copied += __shfl_xor_sync(0xffffffffu, copied, o);
@@ -1658,12 +1658,15 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
         }
         __syncwarp();
         if (al) {
-            for (int u = lane; u < a.nq; u += 32) bulk_g2s(data + S * u, src + NB * u, NB, bar);
+            // consecutive units in pairs: one copy per pair
+            for (int p2 = lane; p2 < a.nq / 2; p2 += 32)
+                bulk_g2s(data + Pol::slot(2 * p2), src + 2 * NB * p2, 2 * NB, bar);
+            if ((a.nq & 1) && lane == 0) bulk_g2s(data + Pol::slot(a.nq - 1), src + NB * (a.nq - 1), NB, bar);
             for (int h = lane; h < a.nhalo; h += 32) {
                 const uint32_t hw = __ldg(a.ring + h);
                 const int32_t tn = __ldg(nrow + (hw >> 24));
                 if (tn >= 0)
-                    bulk_g2s(data + S * (a.nq + h), t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu), NB, bar);
+                    bulk_g2s(data + Pol::slot(a.nq + h), t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu), NB, bar);
             }
         }
     }
@@ -1681,8 +1684,8 @@ __device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, 
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
     const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
     const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
-    uint8_t *tin = stage + 4 * a.nbrw + kStagePad + (Pol::kUnitStride ? 0 : (int)(start & 15));
-    if (Pol::kUnitStride) {
+    uint8_t *tin = stage + 4 * a.nbrw + kStagePad + (Pol::kPadded ? 0 : (int)(start & 15));
+    if (Pol::kPadded) {
         return;   // the whole stage arrives by copies (issue_stage)
     } else if (filler) {
         // the bulk copy covered [cf, ct)
@@ -1799,7 +1802,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         }
         TileIO io = tile_io(a, t, stage, ostage);
         tile_rule<MULTI>(a, Tg, io.rule);
-        if constexpr (Pol::kUnitStride) {
+        if constexpr (Pol::kPadded) {
             // padded units: each thread writes its unit straight to memory
             Pol::compute(a, io, nullptr, tab, R);
         } else {
@@ -1849,7 +1852,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         sn = (sn + 1 == a.nstage) ? 0 : sn + 1;
         if (sn == 0) pn ^= 1u;
     }
-    if (!Pol::kUnitStride && lane == 0) bulk_wait_all();
+    if (!Pol::kPadded && lane == 0) bulk_wait_all();
 }
 
 // Tile loop of the policies that compute from the box: wait for the tile's
@@ -2017,11 +2020,11 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
         fence_proxy_async_smem();
     }
     if constexpr (Pol::kRingInTile) {
-        if constexpr (Pol::kUnitStride) {
+        if constexpr (Pol::kPadded) {
             // the all-zero unit of every stage (no copy ever writes it)
             for (int s = 0; s < a.nstage; ++s)
                 for (int j = tid; j < Pol::NB; j += nth)
-                    smem[s * a.stage_bytes + 4 * a.nbrw + kStagePad + Pol::kUnitStride * a.tapz + j] = 0;
+                    smem[s * a.stage_bytes + 4 * a.nbrw + kStagePad + Pol::slot(a.tapz) + j] = 0;
         }
         if (tid < 32) {
             __syncwarp();
