@@ -170,7 +170,7 @@ def test_nonbinary_input_every_depth(P, fam, r, L):
     assert np.array_equal(out.cpu().numpy(), o.step(raw, rule=oracle_rule(fam), steps=1)), f"L={L}"
 
 
-@pytest.mark.parametrize("fam,r,L", [(W.CARPET, 8, L) for L in (2, 3, 4)] +
+@pytest.mark.parametrize("fam,r,L", [(W.CARPET, 8, L) for L in (2, 3, 4, 5)] +
                          [(W.VICSEK, 9, L) for L in (2, 3, 4, 5, 6)] + [(W.VICSEK, 10, 6)])
 def test_rows_and_lid_policies_many_tiles_per_cta(P, fam, r, L):
     # thousands of tiles per launch: every CTA reuses its stages many times
