@@ -1606,10 +1606,13 @@ __device__ __forceinline__ TileIO tile_io(const StepArgs &a, const TileRef &t, u
     return io;
 }
 
-// Issue the copies of a tile into a stage, by all lanes of one warp: one
-// bulk copy of the tile's bytes, or (policies with padded units) one per
-// unit into its slot.  A unit source that is not 16-byte aligned is copied
-// with plain loads and stores before the stage's mbarrier is armed.
+// 64 zero bytes in device memory, 16-byte aligned: the source of the halo
+// units whose tile is absent (padded-unit policies).
+__device__ __align__(16) uint8_t g_zero_unit[64];
+
+// Issue the copies of a tile into a stage: one bulk copy of the tile's bytes
+// by lane 0 of warp 0, or (policies with padded units, called by every
+// warp) one per pair of units into their slots and one per halo unit.
 template <bool MULTI, class Pol>
 __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t, uint8_t *stage, uint64_t *bar)
 {
@@ -1620,54 +1623,52 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
             issue_tile(a, t, stage, bar);
         }
     } else {
+        // padded units, by every warp of the block: warp w copies the unit
+        // pairs of its 32 units, thread t halo unit t (absent ones from a
+        // unit of zeros in device memory), and thread 0 arms the stage with
+        // the byte count of them all; a buffer that is not 16-byte aligned
+        // is copied with plain loads and stores by warp 0 before it arms
         constexpr int NB = Pol::NB;
+        const int tid = threadIdx.x, warp = tid >> 5;
         const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
         uint8_t *data = stage + row_bytes + kStagePad;
         const uint8_t *src = t.in + t.T * a.KL;
         const int32_t *nrow = t.nbr + t.T * a.nbrw;
         const bool al = ((uintptr_t)src & 15) == 0;
-        // halo units (whole units of the neighbouring tiles) after the tile's
-        // units; those of absent tiles are zeros
-        uint32_t copied = 0;
-        for (int h = lane; h < a.nhalo; h += 32) {
-            const uint32_t hw = __ldg(a.ring + h);
-            const int32_t tn = __ldg(nrow + (hw >> 24));
-            uint8_t *dst = data + Pol::slot(a.nq + h);
-            if (tn < 0) {
-#pragma unroll
-                for (int c = 0; c < NB / 16; ++c) *reinterpret_cast<uint4 *>(dst + 16 * c) = make_uint4(0, 0, 0, 0);
-            } else if (!al) {
-                const uint8_t *hs = t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu);
-                for (int b = 0; b < NB; ++b) dst[b] = hs[b];
-            } else {
-                copied += NB;
-            }
-        }
-        if (!al) {
-            for (int u = lane; u < a.nq; u += 32)
-                for (int b = 0; b < NB; ++b) data[Pol::slot(u) + b] = src[NB * u + b];
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) copied += __shfl_xor_sync(0xffffffffu, copied, o);
-        __threadfence_block();
         fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-            mbar_arrive_expect_tx(bar, row_bytes + (al ? (uint32_t)(a.nq * NB) + copied : 0u));
+        if (!al) {
+            if (warp == 0) {
+                for (int h = lane; h < a.nhalo; h += 32) {
+                    const uint32_t hw = __ldg(a.ring + h);
+                    const int32_t tn = __ldg(nrow + (hw >> 24));
+                    uint8_t *dst = data + Pol::slot(a.nq + h);
+                    const uint8_t *hs = tn < 0 ? g_zero_unit : t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu);
+                    for (int b = 0; b < NB; ++b) dst[b] = hs[b];
+                }
+                for (int u = lane; u < a.nq; u += 32)
+                    for (int b = 0; b < NB; ++b) data[Pol::slot(u) + b] = src[NB * u + b];
+                __threadfence_block();
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(bar, row_bytes);
+                    bulk_g2s(stage, nrow, row_bytes, bar);
+                }
+            }
+            return;
+        }
+        if (tid == 0) {
+            mbar_arrive_expect_tx(bar, row_bytes + (uint32_t)((a.nq + a.nhalo) * NB));
             bulk_g2s(stage, nrow, row_bytes, bar);
         }
-        __syncwarp();
-        if (al) {
-            // consecutive units in pairs: one copy per pair
-            for (int p2 = lane; p2 < a.nq / 2; p2 += 32)
-                bulk_g2s(data + Pol::slot(2 * p2), src + 2 * NB * p2, 2 * NB, bar);
-            if ((a.nq & 1) && lane == 0) bulk_g2s(data + Pol::slot(a.nq - 1), src + NB * (a.nq - 1), NB, bar);
-            for (int h = lane; h < a.nhalo; h += 32) {
-                const uint32_t hw = __ldg(a.ring + h);
-                const int32_t tn = __ldg(nrow + (hw >> 24));
-                if (tn >= 0)
-                    bulk_g2s(data + Pol::slot(a.nq + h), t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu), NB, bar);
-            }
+        for (int p2 = 16 * warp + lane; lane < 16 && p2 < a.nq / 2; p2 += 16 * (int)(blockDim.x >> 5))
+            bulk_g2s(data + Pol::slot(2 * p2), src + 2 * NB * p2, 2 * NB, bar);
+        if ((a.nq & 1) && tid == 32 % (int)blockDim.x) bulk_g2s(data + Pol::slot(a.nq - 1), src + NB * (a.nq - 1), NB, bar);
+        for (int h = tid; h < a.nhalo; h += blockDim.x) {
+            const uint32_t hw = __ldg(a.ring + h);
+            const int32_t tn = __ldg(nrow + (hw >> 24));
+            const uint8_t *hs = tn < 0 ? g_zero_unit : t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu);
+            bulk_g2s(data + Pol::slot(a.nq + h), hs, NB, bar);
         }
     }
 }
@@ -1841,7 +1842,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
             drain_loads(a, bars, i + 1, i + a.nstage - 1);
             break;
         }
-        if (warp == 0) {
+        if (Pol::kPadded || warp == 0) {
             const int64_t Tr = Tg + a.nstage * G;
             if (Tr < a.NT) issue_stage<MULTI, Pol>(a, resolve<MULTI>(a, in, out, Tr), stage, &bars[s]);
         }
@@ -2026,7 +2027,8 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
                 for (int j = tid; j < Pol::NB; j += nth)
                     smem[s * a.stage_bytes + 4 * a.nbrw + kStagePad + Pol::slot(a.tapz) + j] = 0;
         }
-        if (tid < 32) {
+        if (Pol::kPadded) __syncthreads();   // every warp issues: the barriers must be initialised
+        if (Pol::kPadded || tid < 32) {
             __syncwarp();
             for (int s = 0; s < a.nstage; ++s) {
                 const int64_t Tg = blockIdx.x + s * G;
