@@ -25,7 +25,9 @@ struct StepPlan {
     int box_bytes = 0;     // P^dim rounded up to 16
     int coarse_levels = 0; // r - L
     int nring = 0;         // halo cells to fetch per tile
-    int nhalo = 0;         // padded-unit policies: halo units copied whole per tile (ring = their sources)
+    int nhalo = 0;         // padded-unit policies: runs of halo units copied per tile (ring = their sources)
+    int hbytes = 0;        // padded-unit policies: halo bytes copied per tile
+    int zoff = 0;          // padded-unit policies: stage offset of the all-zero unit
     uint32_t *pos = nullptr;   // [KL] box offset of local cell l
     uint32_t *ring = nullptr;  // [2*nring] (box offset | slot << 24, local omega)
     int32_t *nbr = nullptr;    // [NT][nbrw] compact index of each neighbour tile, -1 = none

@@ -290,10 +290,11 @@ struct RowsPolicy {
     struct Regs {
         uint32_t e[8];   // byte offsets of the 8 neighbouring units (W..E, N..S)
     };
-    static_assert(!kPadded || NB == 64, "padded units are 64-byte pairs");
+    static constexpr int kGroup = rp_group<P>();   // units per bulk copy of padded units
+    static_assert(!kPadded || NB == 64, "padded units are 64 bytes");
     __device__ static void init(const StepArgs &a, Regs &R)
     {
-        const int q = threadIdx.x;
+        const int q = rp_thread_unit<P>(threadIdx.x, a.nq);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t w = (q < a.nq) ? __ldg(a.tab + 4 * q + k) : 0u;
@@ -316,8 +317,8 @@ struct RowsPolicy {
     __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *, const uint32_t *,
                                    Regs &R)
     {
-        const int q = threadIdx.x;
-        if (q >= a.nq) return;
+        if ((int)threadIdx.x >= a.nq) return;
+        const int q = rp_thread_unit<P>(threadIdx.x, a.nq);
         uint32_t v[NW];
         uint32_t any = 0;
         if constexpr (kPadded) {

@@ -55,9 +55,10 @@ constexpr int rp_byte(int x, int y)
 }
 
 // Byte offset of unit slot n in a stage.  The carpet's 64-byte units sit in
-// pairs with a 16-byte gap after each pair: 16-byte loads of 8 consecutive
-// units then hit 8 different bank groups (at a plain 64-byte stride every
-// unit would start in one of 2 banks), and one bulk copy brings two units.
+// groups of rp_group consecutive units with a 16-byte gap after each group,
+// so that one bulk copy brings a whole group and the 16-byte loads of the
+// units a quarter-warp handles (rp_thread_unit) hit 8 different bank groups
+// (at a plain 64-byte stride every unit would start in one of 2 of them).
 // The Vicsek fractal's 25-byte units stay contiguous.
 template <int P>
 constexpr bool rp_padded()
@@ -65,9 +66,28 @@ constexpr bool rp_padded()
     return P == 0;
 }
 template <int P>
+constexpr int rp_group()
+{
+    return rp_padded<P>() ? 8 : 1;
+}
+template <int P>
 constexpr int rp_slot(int n)
 {
-    return rp_padded<P>() ? 144 * (n >> 1) + 64 * (n & 1) : RowsPreset<P>::k * RowsPreset<P>::k * n;
+    return rp_padded<P>() ? (64 * rp_group<P>() + 16) * (n / rp_group<P>()) + 64 * (n % rp_group<P>())
+                          : RowsPreset<P>::k * RowsPreset<P>::k * n;
+}
+// The unit thread q handles in a tile of nq units.  For padded units and
+// whole warps of units, lane l of warp w takes unit 32 w + 8 g + 2 h + b
+// with g = (l & 7) >> 1, h = l >> 3, b = l & 1: the 8 lanes of quarter-warp
+// h read from groups g = 0..3 (offsets 16 g mod 128, the group stride being
+// 16 more than 4 x 128) at units 2 h + b of each (64 b mod 128), that is 8
+// distinct 16-byte bank groups.  Otherwise the identity.
+template <int P>
+constexpr int rp_thread_unit(int q, int nq)
+{
+    if (rp_group<P>() != 8 || (nq & 31)) return q;
+    const int l = q & 31;
+    return (q & ~31) + 8 * ((l & 7) >> 1) + 2 * (l >> 3) + (l & 1);
 }
 
 template <int P>

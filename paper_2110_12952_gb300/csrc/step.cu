@@ -60,12 +60,15 @@ namespace fr {
 constexpr int kMaxGroup = 16;  // cells per group / block positions (s^G <= 4)
 constexpr int kQuadKG = 9;     // cells per group in quad mode
 constexpr int kRingRegs = 4;   // halo values per thread prefetched in registers
+constexpr int kRunGap = 2;     // padded units: unneeded units a halo run may span
+constexpr int kRunMax = 8;     // padded units: most units per halo run
 
 struct StepArgs {
     int64_t KL, NT, cells;
     int Px, Py;            // box row pitch and rows per plane (bytes / rows)
     int nring, nbrw, nstage, stage_bytes, tile_bytes;
-    int nhalo;             // padded-unit policies: halo units per tile, sources in `ring`
+    int nhalo;             // padded-unit policies: runs of halo units per tile, in `ring`
+    int hbytes, zoff;      // padded-unit policies: halo bytes per tile, zero unit's stage offset
     int off_bar, off_box, off_tab, off_out, box_bytes;
     int ntab;              // entries of the shared table (cells or groups)
     int KG;                // cells per group (group / quad mode)
@@ -374,15 +377,20 @@ static int rows_preset_of(const fractal *f)
 // Tables of rows mode for tile depth L (>= 2): per unit (level-2 subtree of
 // the tile), the byte offsets (uint16, two per word) of its 8 neighbouring
 // units in the order of frame_dir, from the tile's first cell in the stage:
-// units of the tile at slot u (rp_slot), halo units of neighbouring tiles at
-// slot NU + h, an all-zero unit after them; and the halo bytes to fetch per
-// tile (ring entries as in tap mode), or for padded units the halo units to
-// copy whole.
+// units of the tile at slot u (rp_slot), halo units of neighbouring tiles
+// after them, then an all-zero unit; and the halo bytes to fetch per tile
+// (ring entries as in tap mode), or for padded units the runs of halo units
+// to copy whole.
 struct RowsTables {
     int NU = 0, H = 0;
     std::vector<uint32_t> words;   // NU * 4
     std::vector<uint32_t> ring;    // contiguous units: halo cells (ring entries)
-    std::vector<uint32_t> halo;    // padded units: halo unit h's source, tile-table slot << 24 | unit
+    // padded units: per run of halo units, (tile-table slot << 24 | first
+    // unit, stage offset << 8 | units)
+    std::vector<uint32_t> halo;
+    int hbytes = 0;                // padded units: halo bytes per tile
+    int zoff = 0;                  // stage offset of the zero unit
+    int64_t data_bytes = 0;        // padded units: stage data bytes
     bool ok = false;
 };
 
@@ -449,27 +457,55 @@ static RowsTables rows_tables(const fractal *f, int L)
             nb[(size_t)q * 8 + d] = v;
         }
     t.H = (int)slots.size();
-    const int64_t zero = NU + t.H;
-    if ((int64_t)rp_slot<P>((int)zero) + NB >= 65536) return t;
+    // stage byte offsets of the halo units and of the zero unit
+    std::vector<int> hoff(t.H);
+    int zoff;
+    if constexpr (rp_padded<P>()) {
+        // halo units copied whole, in runs: per neighbouring tile, its
+        // needed units in increasing order, one run spanning gaps of at most
+        // kRunGap unneeded units and at most kRunMax units, the runs back to
+        // back (unpadded: only byte loads read them) after the tile's units
+        std::vector<int> order(t.H);
+        for (int h = 0; h < t.H; ++h) order[h] = h;
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return slots[x] < slots[y]; });
+        const int hb = rp_slot<P>(NU);
+        int pos = hb;
+        for (int i = 0; i < t.H;) {
+            const int ts = slots[order[i]].first, first = slots[order[i]].second;
+            int last = first, j = i + 1;
+            while (j < t.H && slots[order[j]].first == ts && slots[order[j]].second - last <= kRunGap + 1 &&
+                   slots[order[j]].second - first < kRunMax)
+                last = slots[order[j++]].second;
+            for (int m = i; m < j; ++m) hoff[order[m]] = pos + NB * (slots[order[m]].second - first);
+            t.halo.push_back((uint32_t)first | ((uint32_t)ts << 24));
+            t.halo.push_back(((uint32_t)pos << 8) | (uint32_t)(last - first + 1));
+            pos += NB * (last - first + 1);
+            i = j;
+        }
+        t.hbytes = pos - hb;
+        zoff = pos;
+        t.data_bytes = zoff + NB;
+    } else {
+        for (int h = 0; h < t.H; ++h) hoff[h] = rp_slot<P>(NU + h);
+        zoff = rp_slot<P>(NU + t.H);
+    }
+    if ((int64_t)zoff + NB >= 65536) return t;
+    t.zoff = zoff;
     t.words.assign((size_t)NU * 4, 0);
     for (int q = 0; q < NU; ++q)
         for (int d = 0; d < 8; ++d) {
             const int v = nb[(size_t)q * 8 + d];
-            const uint32_t off = (uint32_t)rp_slot<P>(v == -2 ? (int)zero : (v <= -100 ? NU + (-100 - v) : v));
+            const uint32_t off = (uint32_t)(v == -2 ? zoff : (v <= -100 ? hoff[-100 - v] : rp_slot<P>(v)));
             t.words[(size_t)q * 4 + d / 2] |= off << (16 * (d % 2));
         }
-    // padded units: halo units are copied whole; else only the halo bytes
-    // some frame cell reads are staged
-    for (int hs = 0; hs < t.H; ++hs) {
-        if constexpr (rp_padded<P>()) {
-            t.halo.push_back((uint32_t)slots[hs].second | ((uint32_t)slots[hs].first << 24));
-        } else {
+    // contiguous units: only the halo bytes some frame cell reads are staged
+    if constexpr (!rp_padded<P>()) {
+        for (int hs = 0; hs < t.H; ++hs)
             for (int b = 0; b < NB; ++b) {
                 if (!((bytes_read[hs] >> b) & 1u)) continue;
-                t.ring.push_back((uint32_t)(rp_slot<P>(NU + hs) + b) | ((uint32_t)slots[hs].first << 24));
+                t.ring.push_back((uint32_t)(hoff[hs] + b) | ((uint32_t)slots[hs].first << 24));
                 t.ring.push_back((uint32_t)(NB * slots[hs].second + b));
             }
-        }
     }
     t.ok = true;
     return t;
@@ -626,7 +662,7 @@ static Geometry plan_geometry(const fractal *f, int L)
             g.tab_entries = 0;   // the unit tables live in registers
             g.halo = t.H;
             g.halo_bytes = (int64_t)f->k * f->k * (t.H + 1);
-            g.data_bytes = rp_padded<0>() && rp == 0 ? (int64_t)rp_slot<0>(t.NU + t.H + 1) : 0;
+            g.data_bytes = t.data_bytes;
             g.block = std::max<int64_t>(64, ((int64_t)t.NU + 31) / 32 * 32);
             g.box_bytes = 0;
             return g;
@@ -843,7 +879,9 @@ int ensure_step_plan(fractal *f)
         p.nq = t.NU;
         tab = t.words;
         ring = t.halo.empty() ? t.ring : t.halo;
-        p.nhalo = (int)t.halo.size();
+        p.nhalo = (int)t.halo.size() / 2;
+        p.hbytes = t.hbytes;
+        p.zoff = t.zoff;
     } else {
         // local lambda -> padded box offset; occupancy of the interior
         std::vector<uint32_t> pos(p.KL);
@@ -1606,13 +1644,14 @@ __device__ __forceinline__ TileIO tile_io(const StepArgs &a, const TileRef &t, u
     return io;
 }
 
-// 64 zero bytes in device memory, 16-byte aligned: the source of the halo
-// units whose tile is absent (padded-unit policies).
-__device__ __align__(16) uint8_t g_zero_unit[64];
+// Zero bytes in device memory, 16-byte aligned: the source of the halo
+// runs whose tile is absent (padded-unit policies, runs of <= kRunMax units).
+__device__ __align__(16) uint8_t g_zero_run[64 * kRunMax];
 
 // Issue the copies of a tile into a stage: one bulk copy of the tile's bytes
 // by lane 0 of warp 0, or (policies with padded units, called by every
-// warp) one per pair of units into their slots and one per halo unit.
+// warp) one per group of units into their slots and one per run of halo
+// units.
 template <bool MULTI, class Pol>
 __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t, uint8_t *stage, uint64_t *bar)
 {
@@ -1623,11 +1662,14 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
             issue_tile(a, t, stage, bar);
         }
     } else {
-        // padded units, by every warp of the block: warp w copies the unit
-        // pairs of its 32 units, thread t halo unit t (absent ones from a
-        // unit of zeros in device memory), and thread 0 arms the stage with
-        // the byte count of them all; a buffer that is not 16-byte aligned
-        // is copied with plain loads and stores by warp 0 before it arms
+        // padded units, by every warp of the block: lane l < 16 of warp w
+        // copies unit groups 16 w + l, 16 (w + warps) + l, ... (the units
+        // past the last whole group one by one, by threads 32 on), thread t
+        // halo run t (absent ones from zeros in device memory), and thread
+        // 0 arms the stage with the byte count of them all; a buffer that
+        // is not 16-byte aligned is copied with plain loads and stores by
+        // warp 0 before it arms
+        static_assert(Pol::NB * kRunMax <= (int)sizeof(g_zero_run), "zero run");
         constexpr int NB = Pol::NB;
         const int tid = threadIdx.x, warp = tid >> 5;
         const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
@@ -1639,11 +1681,11 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
         if (!al) {
             if (warp == 0) {
                 for (int h = lane; h < a.nhalo; h += 32) {
-                    const uint32_t hw = __ldg(a.ring + h);
-                    const int32_t tn = __ldg(nrow + (hw >> 24));
-                    uint8_t *dst = data + Pol::slot(a.nq + h);
-                    const uint8_t *hs = tn < 0 ? g_zero_unit : t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu);
-                    for (int b = 0; b < NB; ++b) dst[b] = hs[b];
+                    const uint32_t w0 = __ldg(a.ring + 2 * h), w1 = __ldg(a.ring + 2 * h + 1);
+                    const int32_t tn = __ldg(nrow + (w0 >> 24));
+                    uint8_t *dst = data + (w1 >> 8);
+                    const uint8_t *hs = tn < 0 ? g_zero_run : t.in + (int64_t)tn * a.KL + (int64_t)NB * (w0 & 0xffffffu);
+                    for (int b = 0; b < NB * (int)(w1 & 0xffu); ++b) dst[b] = hs[b];
                 }
                 for (int u = lane; u < a.nq; u += 32)
                     for (int b = 0; b < NB; ++b) data[Pol::slot(u) + b] = src[NB * u + b];
@@ -1658,17 +1700,22 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
             return;
         }
         if (tid == 0) {
-            mbar_arrive_expect_tx(bar, row_bytes + (uint32_t)((a.nq + a.nhalo) * NB));
+            mbar_arrive_expect_tx(bar, row_bytes + (uint32_t)(a.nq * NB + a.hbytes));
             bulk_g2s(stage, nrow, row_bytes, bar);
         }
-        for (int p2 = 16 * warp + lane; lane < 16 && p2 < a.nq / 2; p2 += 16 * (int)(blockDim.x >> 5))
-            bulk_g2s(data + Pol::slot(2 * p2), src + 2 * NB * p2, 2 * NB, bar);
-        if ((a.nq & 1) && tid == 32 % (int)blockDim.x) bulk_g2s(data + Pol::slot(a.nq - 1), src + NB * (a.nq - 1), NB, bar);
+        constexpr int G = Pol::kGroup;
+        const int ng = a.nq / G, rem = a.nq - G * ng;
+        for (int p = 16 * warp + lane; lane < 16 && p < ng; p += 16 * (int)(blockDim.x >> 5))
+            bulk_g2s(data + Pol::slot(G * p), src + G * NB * p, G * NB, bar);
+        if (tid >= 32 && tid < 32 + rem) {
+            const int u = G * ng + tid - 32;
+            bulk_g2s(data + Pol::slot(u), src + NB * u, NB, bar);
+        }
         for (int h = tid; h < a.nhalo; h += blockDim.x) {
-            const uint32_t hw = __ldg(a.ring + h);
-            const int32_t tn = __ldg(nrow + (hw >> 24));
-            const uint8_t *hs = tn < 0 ? g_zero_unit : t.in + (int64_t)tn * a.KL + (int64_t)NB * (hw & 0xffffffu);
-            bulk_g2s(data + Pol::slot(a.nq + h), hs, NB, bar);
+            const uint32_t w0 = __ldg(a.ring + 2 * h), w1 = __ldg(a.ring + 2 * h + 1);
+            const int32_t tn = __ldg(nrow + (w0 >> 24));
+            const uint8_t *hs = tn < 0 ? g_zero_run : t.in + (int64_t)tn * a.KL + (int64_t)NB * (w0 & 0xffffffu);
+            bulk_g2s(data + (w1 >> 8), hs, (uint32_t)NB * (w1 & 0xffu), bar);
         }
     }
 }
@@ -1686,8 +1733,8 @@ __device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, 
     const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
     const uintptr_t start = (uintptr_t)(t.in + t.T * a.KL);
     uint8_t *tin = stage + 4 * a.nbrw + kStagePad + (Pol::kPadded ? 0 : (int)(start & 15));
-    if (Pol::kPadded) {
-        return;   // the whole stage arrives by copies (issue_stage)
+    if constexpr (Pol::kPadded) {
+        // the tile's units and halo units arrive by copies (issue_stage)
     } else if (filler) {
         // the bulk copy covered [cf, ct)
         const uintptr_t end = start + (uintptr_t)a.KL;
@@ -2025,7 +2072,7 @@ step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *
             // the all-zero unit of every stage (no copy ever writes it)
             for (int s = 0; s < a.nstage; ++s)
                 for (int j = tid; j < Pol::NB; j += nth)
-                    smem[s * a.stage_bytes + 4 * a.nbrw + kStagePad + Pol::slot(a.tapz) + j] = 0;
+                    smem[s * a.stage_bytes + 4 * a.nbrw + kStagePad + a.zoff + j] = 0;
         }
         if (Pol::kPadded) __syncthreads();   // every warp issues: the barriers must be initialised
         if (Pol::kPadded || tid < 32) {
@@ -2098,6 +2145,8 @@ static void fill_args(const fractal *f, StepArgs &a)
     a.Py = p.Py;
     a.nring = p.nring;
     a.nhalo = p.nhalo;
+    a.hbytes = p.hbytes;
+    a.zoff = p.zoff;
     a.nbrw = p.nbrw;
     a.nstage = p.nstage;
     a.stage_bytes = p.stage_bytes;
