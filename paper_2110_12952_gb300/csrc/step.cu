@@ -1648,12 +1648,29 @@ __device__ __forceinline__ TileIO tile_io(const StepArgs &a, const TileRef &t, u
 // runs whose tile is absent (padded-unit policies, runs of <= kRunMax units).
 __device__ __align__(16) uint8_t g_zero_run[64 * kRunMax];
 
+// A thread's first run of halo units (padded-unit policies): its two table
+// words and, when `pre`, the table entry of its neighbouring tile for the
+// tile about to be issued, loaded ahead of time.
+struct HaloRun {
+    uint32_t w0, w1;
+    int32_t tn;
+    bool pre;
+};
+// The first halo run of thread tid: the last warp's threads take the runs
+// first, so that warp 0 (which arms the stage and copies the unit groups)
+// and the last warp share the issue work.
+__device__ __forceinline__ int first_halo_run(int tid, int nth)
+{
+    return tid + 32 < nth ? tid + 32 : tid + 32 - nth;
+}
+
 // Issue the copies of a tile into a stage: one bulk copy of the tile's bytes
 // by lane 0 of warp 0, or (policies with padded units, called by every
 // warp) one per group of units into their slots and one per run of halo
-// units.
+// units (`hr`: this thread's first run, or null).
 template <bool MULTI, class Pol>
-__device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t, uint8_t *stage, uint64_t *bar)
+__device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t, uint8_t *stage, uint64_t *bar,
+                                            const HaloRun *hr = nullptr)
 {
     const int lane = threadIdx.x & 31;
     if constexpr (!Pol::kPadded) {
@@ -1664,11 +1681,11 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
     } else {
         // padded units, by every warp of the block: lane l < 16 of warp w
         // copies unit groups 16 w + l, 16 (w + warps) + l, ... (the units
-        // past the last whole group one by one, by threads 32 on), thread t
-        // halo run t (absent ones from zeros in device memory), and thread
-        // 0 arms the stage with the byte count of them all; a buffer that
-        // is not 16-byte aligned is copied with plain loads and stores by
-        // warp 0 before it arms
+        // past the last whole group one by one, by threads 32 on), each
+        // thread its halo runs (first_halo_run on, absent ones from zeros
+        // in device memory), and thread 0 arms the stage with the byte count
+        // of them all; a buffer that is not 16-byte aligned is copied with
+        // plain loads and stores by warp 0 before it arms
         static_assert(Pol::NB * kRunMax <= (int)sizeof(g_zero_run), "zero run");
         constexpr int NB = Pol::NB;
         const int tid = threadIdx.x, warp = tid >> 5;
@@ -1711,9 +1728,19 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
             const int u = G * ng + tid - 32;
             bulk_g2s(data + Pol::slot(u), src + NB * u, NB, bar);
         }
-        for (int h = tid; h < a.nhalo; h += blockDim.x) {
-            const uint32_t w0 = __ldg(a.ring + 2 * h), w1 = __ldg(a.ring + 2 * h + 1);
-            const int32_t tn = __ldg(nrow + (w0 >> 24));
+        const int h0 = first_halo_run(tid, blockDim.x);
+        for (int h = h0; h < a.nhalo; h += blockDim.x) {
+            uint32_t w0, w1;
+            int32_t tn;
+            if (h == h0 && hr) {
+                w0 = hr->w0;
+                w1 = hr->w1;
+                tn = hr->pre ? hr->tn : __ldg(nrow + (w0 >> 24));
+            } else {
+                w0 = __ldg(a.ring + 2 * h);
+                w1 = __ldg(a.ring + 2 * h + 1);
+                tn = __ldg(nrow + (w0 >> 24));
+            }
             const uint8_t *hs = tn < 0 ? g_zero_run : t.in + (int64_t)tn * a.KL + (int64_t)NB * (w0 & 0xffffffu);
             bulk_g2s(data + (w1 >> 8), hs, (uint32_t)NB * (w1 & 0xffu), bar);
         }
@@ -1807,6 +1834,12 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
     uint32_t rv[kRingRegs];   // prefetched halo values of the next tile
 #pragma unroll
     for (int k = 0; k < kRingRegs; ++k) rv[k] = 0;
+    HaloRun hr{0u, 0u, 0, false};   // padded units: this thread's first halo run
+    const bool has_run = Pol::kPadded && first_halo_run(tid, blockDim.x) < a.nhalo;
+    if (has_run) {
+        hr.w0 = __ldg(a.ring + 2 * first_halo_run(tid, blockDim.x));
+        hr.w1 = __ldg(a.ring + 2 * first_halo_run(tid, blockDim.x) + 1);
+    }
     TileRef t = resolve<MULTI>(a, in, out, Tg);
     bool ok = mbar_wait_bounded(&bars[0], 0);
     if (ok) fill_stage<MULTI, Pol>(a, t, smem, filler, rv, false);
@@ -1847,6 +1880,17 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
                 }
             }
             pref = true;
+        }
+        if constexpr (Pol::kPadded) {
+            // the neighbouring tile of this thread's halo run for the tile
+            // this stage is refilled with, loaded before the compute so that
+            // the refill does not wait for it
+            const int64_t Tr = Tg + a.nstage * G;
+            if (has_run && Tr < a.NT) {
+                const TileRef r = resolve<MULTI>(a, in, out, Tr);
+                hr.tn = __ldg(r.nbr + r.T * a.nbrw + (hr.w0 >> 24));
+                hr.pre = true;
+            }
         }
         TileIO io = tile_io(a, t, stage, ostage);
         tile_rule<MULTI>(a, Tg, io.rule);
@@ -1891,7 +1935,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         }
         if (Pol::kPadded || warp == 0) {
             const int64_t Tr = Tg + a.nstage * G;
-            if (Tr < a.NT) issue_stage<MULTI, Pol>(a, resolve<MULTI>(a, in, out, Tr), stage, &bars[s]);
+            if (Tr < a.NT) issue_stage<MULTI, Pol>(a, resolve<MULTI>(a, in, out, Tr), stage, &bars[s], &hr);
         }
         if (!has_next) break;
         Tg = Tn;
