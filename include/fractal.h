@@ -183,7 +183,8 @@ int fractal_get_tile_levels(const fractal_t *f, int *levels);
  * groups of s^G x s^G cells, 9: 2D groups of 9 cells in a shared-memory
  * box, 10: the triangle's 81-cell units with taps, 11 / 12: the carpet's /
  * Vicsek fractal's level-2 units summed by rows, 13: the Vicsek fractal's
- * level-3 units summed in omega order), the tile depth L,
+ * level-3 units summed in omega order, 14: a 3D tile's box summed by whole
+ * rows, then gathered in omega order), the tile depth L,
  * threads per block, blocks per launch, dynamic shared memory bytes per
  * block, input pipeline stages, and resident blocks per SM.  1 <= n <= 7,
  * else FR_EINVAL. */

@@ -145,7 +145,15 @@ static int group_levels(const fractal *f)
     return 0;
 }
 
-enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10, kModeRows0 = 11, kModeRows1 = 12, kModeLid1 = 13 };
+enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10, kModeRows0 = 11, kModeRows1 = 12, kModeLid1 = 13,
+       kModeBox3 = 14 };
+
+// ---- box3 mode (3D fractals, see box3.cuh): box row pitch, a multiple of
+// 16 bytes with at least one zero word after the B + 2 padded cells
+static int64_t box3_pitch(int64_t B)
+{
+    return (4 * ((B + 3) / 4) + 4 + 15) / 16 * 16;
+}
 
 // ---- tap mode: the Sierpinski triangle with offsets (0,0), (1,0), (0,1)
 // A level-2 group is 9 cells (lid 0..8 at kPosX/kPosY) filling a 4x4 block.
@@ -668,6 +676,19 @@ static Geometry plan_geometry(const fractal *f, int L)
             return g;
         }
     }
+    if (f->dim == 3) {
+        const int64_t Px = box3_pitch(g.B), vol = Px * (g.B + 2) * (g.B + 2);
+        if (Px <= 64 && vol < 65536) {
+            g.mode = kModeBox3;
+            g.G = 0;
+            g.Px = Px;
+            g.Py = g.B + 2;
+            g.planes = g.B + 2;
+            g.tab_entries = (ipow(f->k, L) + 3) / 4 * 2;   // 16-bit box offsets, two per word
+            g.box_bytes = 2 * round16(vol + 16);            // the box, then the totals box
+            return g;
+        }
+    }
     if (grp) {
         g.mode = (int)ipow(f->s, g.G);
         g.tab_entries = ipow(f->k, L - g.G);
@@ -710,7 +731,7 @@ static Layout plan_layout(const fractal *f, int L)
     Geometry g = plan_geometry(f, L);
     int64_t KL = ipow(f->k, L);
     y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1 ||
-                g.mode == kModeLid1) ? 2 : nstages();
+                g.mode == kModeLid1 || g.mode == kModeBox3) ? 2 : nstages();
     // slack: 16-byte rounding of the bulk copy, whole-word reads and writes
     // past the tile's last cell; tap mode: halo and zero groups
     y.tile_bytes = round16((g.data_bytes > 0 ? g.data_bytes : KL + g.halo_bytes) + 64);
@@ -894,7 +915,10 @@ int ensure_step_plan(fractal *f)
             pos[l] = (uint32_t)o;
             occ[o] = 1;
         }
-        if (p.mode != kModeCell) {
+        if (p.mode == kModeBox3) {
+            tab.assign(geo.tab_entries, 0u);
+            for (int64_t l = 0; l < p.KL; ++l) tab[l / 2] |= pos[l] << (16 * (l % 2));
+        } else if (p.mode != kModeCell) {
             // group g = cells [g k^G, (g+1) k^G); its block sits at s^G * (coarse
             // lambda of g over L - G levels); the window starts one cell up-left
             const int KG = (int)ipow(f->k, p.G), SG = (int)ipow(f->s, p.G);
@@ -1010,7 +1034,7 @@ int ensure_step_plan(fractal *f)
         FR_CUDA(cudaGetLastError());
         FR_CUDA(cudaDeviceSynchronize());
     }
-    if (dim == 3) rc = configure<3, kModeCell>(p, f->num_sms);
+    if (dim == 3) rc = p.mode == kModeBox3 ? configure<3, kModeBox3>(p, f->num_sms) : configure<3, kModeCell>(p, f->num_sms);
     else if (p.mode == kModeQuad) rc = configure<2, kModeQuad>(p, f->num_sms);
     else if (p.mode == kModeTap) rc = configure<2, kModeTap>(p, f->num_sms);
     else if (p.mode == kModeRows0) rc = configure<2, kModeRows0>(p, f->num_sms);
@@ -1534,6 +1558,7 @@ struct TapPolicy {
 }  // namespace fr
 #include "rows.cuh"
 #include "lid.cuh"
+#include "box3.cuh"
 namespace fr {
 
 template <int DIM, int MODE>
@@ -1554,6 +1579,8 @@ template <>
 struct PolicyOf<2, kModeRows1> { using type = RowsPolicy<1>; };
 template <>
 struct PolicyOf<2, kModeLid1> { using type = LidPolicy<kLidPreset, kLidLevels>; };
+template <>
+struct PolicyOf<3, kModeBox3> { using type = Box3Policy; };
 
 // A tile of the launch resolved to its instance's buffers, table and rule.
 struct TileRef {
@@ -2096,7 +2123,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
 }
 
 template <int DIM, int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, MODE == kModeTap || MODE == kModeRows0 || MODE == kModeRows1 || MODE == kModeLid1 ? 3 : 4)
+__global__ void __launch_bounds__(256, MODE == kModeBox3 ? 2 : (MODE == kModeTap || MODE == kModeRows0 || MODE == kModeRows1 || MODE == kModeLid1 ? 3 : 4))
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     using Pol = typename PolicyOf<DIM, MODE>::type;
@@ -2224,7 +2251,9 @@ static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t
                     cudaStream_t st)
 {
     const StepPlan &p = f->plan;
-    if (f->dim == 3)
+    if (f->dim == 3 && p.mode == kModeBox3)
+        step_tma_kernel<3, kModeBox3, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
+    else if (f->dim == 3)
         step_tma_kernel<3, kModeCell, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (p.mode == kModeQuad)
         step_tma_kernel<2, kModeQuad, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);

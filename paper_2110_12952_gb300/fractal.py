@@ -156,7 +156,7 @@ class Fractal:
     def tile_levels(self, levels: int):
         self._check(self._lib.fractal_set_tile_levels(self._h, int(levels)))
 
-    POLICIES = {0: "cell", 3: "group3", 4: "group4", 9: "quad", 10: "tap", 11: "rows_carpet", 12: "rows_vicsek", 13: "lid_vicsek"}
+    POLICIES = {0: "cell", 3: "group3", 4: "group4", 9: "quad", 10: "tap", 11: "rows_carpet", 12: "rows_vicsek", 13: "lid_vicsek", 14: "box3"}
 
     def plan_info(self) -> dict:
         """The step's launch plan (``fractal_plan_info``)."""

@@ -158,7 +158,8 @@ def test_triangle_many_tiles_per_cta(P, L):
 
 
 @pytest.mark.parametrize("fam,r,L", [(W.TRIANGLE, 12, L) for L in range(2, 10)] +
-                         [(W.CARPET, 6, L) for L in range(1, 6)] + [(W.VICSEK, 7, L) for L in range(1, 6)])
+                         [(W.CARPET, 6, L) for L in range(1, 6)] + [(W.VICSEK, 7, L) for L in range(1, 6)] +
+                         [(W.MENGER, 4, L) for L in range(0, 4)])
 def test_nonbinary_input_every_depth(P, fam, r, L):
     # any nonzero byte is alive: the first generation must read 0..255 as
     # 0/1 wherever a cell is read (own cells, taps, frames, halo)
@@ -171,14 +172,16 @@ def test_nonbinary_input_every_depth(P, fam, r, L):
 
 
 @pytest.mark.parametrize("fam,r,L", [(W.CARPET, 8, L) for L in (2, 3, 4, 5)] +
-                         [(W.VICSEK, 9, L) for L in (2, 3, 4, 5, 6)] + [(W.VICSEK, 10, 6)])
+                         [(W.VICSEK, 9, L) for L in (2, 3, 4, 5, 6)] + [(W.VICSEK, 10, 6)] +
+                         [(W.MENGER, 5, L) for L in (2, 3)])
 def test_rows_and_lid_policies_many_tiles_per_cta(P, fam, r, L):
     # thousands of tiles per launch: every CTA reuses its stages many times
     g, o = gpu_fr(P, fam, r), ora(fam, r)
     init = o.init_bernoulli(9, 0.5)
     g.tile_levels = L
-    out = g.step(torch.from_numpy(init).cuda(), steps=3, rule=rule_of(fam))
-    assert np.array_equal(out.cpu().numpy(), o.step(init, rule=oracle_rule(fam), steps=3)), f"L={L}"
+    steps = 2 if fam.dim == 3 else 3
+    out = g.step(torch.from_numpy(init).cuda(), steps=steps, rule=rule_of(fam))
+    assert np.array_equal(out.cpu().numpy(), o.step(init, rule=oracle_rule(fam), steps=steps)), f"L={L}"
 
 
 def test_autotune_keeps_parity(P):
@@ -374,6 +377,11 @@ def test_plan_info(P):
     assert vi["policy_name"] == "lid_vicsek" and vi["block"] == 128   # 5^3 units of 125 cells
     v.tile_levels = 2
     assert v.plan_info()["policy_name"] == "rows_vicsek"
+    m = gpu_fr(P, W.MENGER, 4)
+    m.tile_levels = 3
+    mi = m.plan_info()
+    # a 27^3 box in 32-byte rows, its totals box and 16-bit offsets: two stages, two CTAs per SM
+    assert mi["policy_name"] == "box3" and mi["stages"] == 2 and mi["smem_bytes"] <= 100 * 1024
     arr = (ctypes.c_int32 * 8)()
     assert g._lib.fractal_plan_info(g._h, arr, 0) != 0
     assert g._lib.fractal_plan_info(g._h, arr, 8) != 0
