@@ -16,51 +16,52 @@
 
 namespace fr {
 
-// Totals of the box row at byte offset `off` (an interior row: 1 <= y, z <=
-// B): the column sums over the 9 rows (y + dy, z + dz) in NWR words, then
-// for box position 4w + j the sum of columns 4w + j - 1 .. 4w + j + 1 from
-// words w - 1, w, w + 1 with funnel shifts.  Bytes stay <= 27: no carries.
-template <int NWR>
-__device__ __forceinline__ void box3_row(const uint8_t *box, uint8_t *tbox, int off, int Px, int PxPy)
-{
-    uint32_t V[NWR];
-#pragma unroll
-    for (int w = 0; w < NWR; ++w) V[w] = 0;
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            const uint4 *rp = reinterpret_cast<const uint4 *>(box + off + dy * Px + dz * PxPy);
-#pragma unroll
-            for (int c = 0; c < NWR / 4; ++c) {
-                const uint4 q = rp[c];
-                V[4 * c] += q.x;
-                V[4 * c + 1] += q.y;
-                V[4 * c + 2] += q.z;
-                V[4 * c + 3] += q.w;
-            }
-        }
-    uint4 *tp = reinterpret_cast<uint4 *>(tbox + off);
-#pragma unroll
-    for (int c = 0; c < NWR / 4; ++c) {
-        uint32_t T[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int w = 4 * c + j;
-            const uint32_t prev = (w > 0) ? V[w - 1] : 0u, next = (w + 1 < NWR) ? V[w + 1] : 0u;
-            T[j] = __funnelshift_r(prev, V[w], 24) + V[w] + __funnelshift_r(V[w], next, 8);
-        }
-        tp[c] = make_uint4(T[0], T[1], T[2], T[3]);
-    }
-}
-
-template <int NWR>
+// Totals of the interior box rows (1 <= y, z <= B), NC 16-byte chunks per
+// row: a team of TEAM >= NC consecutive lanes takes a row, lane c of it
+// chunk c (so that the 8 lanes of a quarter-warp read 8 different 16-byte
+// bank groups).  Each lane sums its chunk over the 9 rows (y + dy, z + dz)
+// (column sums, <= 9 per byte), gets the last column sum of chunk c - 1 and
+// the first of chunk c + 1 from its team neighbours, and forms for box
+// position 4w + j the sum of column sums 4w + j - 1 .. 4w + j + 1 with
+// funnel shifts (<= 27 per byte: no carries).
+template <int NC, int TEAM>
 __device__ __forceinline__ void box3_rows(const StepArgs &a, const uint8_t *box, uint8_t *tbox)
 {
-    const int B = a.Py - 2, Px = a.Px, PxPy = a.Px * a.Py;
-    for (int i = threadIdx.x; i < B * B; i += blockDim.x) {
-        const int y = 1 + i % B, z = 1 + i / B;
-        box3_row<NWR>(box, tbox, Px * y + PxPy * z, Px, PxPy);
+    const int B = a.Py - 2, Px = a.Px, PxPy = a.Px * a.Py, rows = B * B;
+    const int tid = threadIdx.x, c = tid % TEAM;
+    for (int r0 = 0; r0 < rows; r0 += (int)blockDim.x / TEAM) {
+        const int r = r0 + tid / TEAM;
+        const bool valid = r < rows && c < NC;
+        const int off = valid ? Px * (1 + r % B) + PxPy * (1 + r / B) + 16 * c : 0;
+        uint32_t V[4] = {0u, 0u, 0u, 0u};
+        if (valid) {
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(box + off + dy * Px + dz * PxPy);
+                    V[0] += q.x;
+                    V[1] += q.y;
+                    V[2] += q.z;
+                    V[3] += q.w;
+                }
+        }
+        uint32_t prev = 0u, next = 0u;
+        if constexpr (TEAM > 1) {
+            prev = __shfl_up_sync(0xffffffffu, V[3], 1, TEAM);
+            next = __shfl_down_sync(0xffffffffu, V[0], 1, TEAM);
+            if (c == 0) prev = 0u;
+            if (c + 1 >= NC) next = 0u;
+        }
+        if (valid) {
+            uint32_t T[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t lo = (w > 0) ? V[w - 1] : prev, hi = (w < 3) ? V[w + 1] : next;
+                T[w] = __funnelshift_r(lo, V[w], 24) + V[w] + __funnelshift_r(V[w], hi, 8);
+            }
+            *reinterpret_cast<uint4 *>(tbox + off) = make_uint4(T[0], T[1], T[2], T[3]);
+        }
     }
 }
 
@@ -78,16 +79,17 @@ struct Box3Policy {
                                    Regs &)
     {
         uint8_t *tbox = const_cast<uint8_t *>(box) + a.box_bytes / 2;
-        switch (a.Px >> 2) {
-            case 4: box3_rows<4>(a, box, tbox); break;
-            case 8: box3_rows<8>(a, box, tbox); break;
-            case 12: box3_rows<12>(a, box, tbox); break;
-            default: box3_rows<16>(a, box, tbox); break;
+        switch (a.Px >> 4) {
+            case 1: box3_rows<1, 1>(a, box, tbox); break;
+            case 2: box3_rows<2, 2>(a, box, tbox); break;
+            case 3: box3_rows<3, 4>(a, box, tbox); break;
+            default: box3_rows<4, 4>(a, box, tbox); break;
         }
         __syncthreads();
         // four consecutive cells per thread: their box offsets in one 8-byte
-        // load, total and state from the boxes; a live cell's total counts
-        // itself, hence the survival mask shifted up by one
+        // load, state and total from the two boxes (the input stage is being
+        // refilled by now); a live cell's total counts itself, hence the
+        // survival mask shifted up by one
         const uint16_t *tab16 = reinterpret_cast<const uint16_t *>(tab);
         uint8_t *tout = io.ostage + io.a_out;
         const uint32_t live = io.rule.survive << 1, dead = io.rule.birth;
