@@ -17,50 +17,70 @@
 namespace fr {
 
 // Totals of the interior box rows (1 <= y, z <= B), NC 16-byte chunks per
-// row: a team of TEAM >= NC consecutive lanes takes a row, lane c of it
-// chunk c (so that the 8 lanes of a quarter-warp read 8 different 16-byte
-// bank groups).  Each lane sums its chunk over the 9 rows (y + dy, z + dz)
-// (column sums, <= 9 per byte), gets the last column sum of chunk c - 1 and
-// the first of chunk c + 1 from its team neighbours, and forms for box
-// position 4w + j the sum of column sums 4w + j - 1 .. 4w + j + 1 with
-// funnel shifts (<= 27 per byte: no carries).
-template <int NC, int TEAM>
+// row.  A team of TEAM >= NC consecutive lanes takes the rows y0 .. y0 +
+// S - 1 of plane z, lane c of it chunk c (so that the 8 lanes of a
+// quarter-warp read 8 different 16-byte bank groups).  Sliding down y, each
+// lane keeps the plane sums P(y) = row(y, z - 1) + row(y, z) + row(y, z +
+// 1) of its chunk for three rows, so that the column sums V(y) = P(y - 1) +
+// P(y) + P(y + 1) (<= 9 per byte) cost three row loads each; it gets the
+// last column sum of chunk c - 1 and the first of chunk c + 1 from its team
+// neighbours and forms for box position 4w + j the sum of column sums
+// 4w + j - 1 .. 4w + j + 1 with funnel shifts (<= 27 per byte: no carries).
+template <int NC, int TEAM, int S>
 __device__ __forceinline__ void box3_rows(const StepArgs &a, const uint8_t *box, uint8_t *tbox)
 {
-    const int B = a.Py - 2, Px = a.Px, PxPy = a.Px * a.Py, rows = B * B;
+    const int B = a.Py - 2, Px = a.Px, PxPy = a.Px * a.Py, nseg = (B + S - 1) / S, items = B * nseg;
     const int tid = threadIdx.x, c = tid % TEAM;
-    for (int r0 = 0; r0 < rows; r0 += (int)blockDim.x / TEAM) {
-        const int r = r0 + tid / TEAM;
-        const bool valid = r < rows && c < NC;
-        const int off = valid ? Px * (1 + r % B) + PxPy * (1 + r / B) + 16 * c : 0;
-        uint32_t V[4] = {0u, 0u, 0u, 0u};
-        if (valid) {
+    for (int i0 = 0; i0 < items; i0 += (int)blockDim.x / TEAM) {
+        const int it = i0 + tid / TEAM;
+        const bool lane_ok = it < items && c < NC;
+        const int z = 1 + it % B, y0 = 1 + S * (it / B);
+        // byte offset of (y0, z), chunk c; only rows y <= B are stored
+        const int base = lane_ok ? Px * y0 + PxPy * z + 16 * c : 0;
+        auto plane_sum = [&](int dy, uint32_t *P) {
+            P[0] = P[1] = P[2] = P[3] = 0u;
+            if (lane_ok && y0 + dy <= B + 1) {   // rows past the box only feed rows past B
 #pragma unroll
-            for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const uint4 q = *reinterpret_cast<const uint4 *>(box + off + dy * Px + dz * PxPy);
-                    V[0] += q.x;
-                    V[1] += q.y;
-                    V[2] += q.z;
-                    V[3] += q.w;
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(box + base + dy * Px + dz * PxPy);
+                    P[0] += q.x;
+                    P[1] += q.y;
+                    P[2] += q.z;
+                    P[3] += q.w;
                 }
-        }
-        uint32_t prev = 0u, next = 0u;
-        if constexpr (TEAM > 1) {
-            prev = __shfl_up_sync(0xffffffffu, V[3], 1, TEAM);
-            next = __shfl_down_sync(0xffffffffu, V[0], 1, TEAM);
-            if (c == 0) prev = 0u;
-            if (c + 1 >= NC) next = 0u;
-        }
-        if (valid) {
-            uint32_t T[4];
+            }
+        };
+        uint32_t Pa[4], Pb[4];
+        plane_sum(-1, Pa);
+        plane_sum(0, Pb);
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            uint32_t Pc[4];
+            plane_sum(k + 1, Pc);
+            uint32_t V[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) V[w] = Pa[w] + Pb[w] + Pc[w];
+            uint32_t prev = 0u, next = 0u;
+            if constexpr (TEAM > 1) {
+                prev = __shfl_up_sync(0xffffffffu, V[3], 1, TEAM);
+                next = __shfl_down_sync(0xffffffffu, V[0], 1, TEAM);
+                if (c == 0) prev = 0u;
+                if (c + 1 >= NC) next = 0u;
+            }
+            if (lane_ok && y0 + k <= B) {
+                uint32_t T[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t lo = (w > 0) ? V[w - 1] : prev, hi = (w < 3) ? V[w + 1] : next;
+                    T[w] = __funnelshift_r(lo, V[w], 24) + V[w] + __funnelshift_r(V[w], hi, 8);
+                }
+                *reinterpret_cast<uint4 *>(tbox + base + k * Px) = make_uint4(T[0], T[1], T[2], T[3]);
+            }
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
-                const uint32_t lo = (w > 0) ? V[w - 1] : prev, hi = (w < 3) ? V[w + 1] : next;
-                T[w] = __funnelshift_r(lo, V[w], 24) + V[w] + __funnelshift_r(V[w], hi, 8);
+                Pa[w] = Pb[w];
+                Pb[w] = Pc[w];
             }
-            *reinterpret_cast<uint4 *>(tbox + off) = make_uint4(T[0], T[1], T[2], T[3]);
         }
     }
 }
@@ -80,10 +100,10 @@ struct Box3Policy {
     {
         uint8_t *tbox = const_cast<uint8_t *>(box) + a.box_bytes / 2;
         switch (a.Px >> 4) {
-            case 1: box3_rows<1, 1>(a, box, tbox); break;
-            case 2: box3_rows<2, 2>(a, box, tbox); break;
-            case 3: box3_rows<3, 4>(a, box, tbox); break;
-            default: box3_rows<4, 4>(a, box, tbox); break;
+            case 1: box3_rows<1, 1, 3>(a, box, tbox); break;
+            case 2: box3_rows<2, 2, 3>(a, box, tbox); break;
+            case 3: box3_rows<3, 4, 3>(a, box, tbox); break;
+            default: box3_rows<4, 4, 3>(a, box, tbox); break;
         }
         __syncthreads();
         // four consecutive cells per thread: their box offsets in one 8-byte
