@@ -254,6 +254,19 @@ def time_steps(fn, steps, warmup, flush=None):
     return times
 
 
+def aggregate_ranks(ms_local, units_local, world, dist, device):
+    """Whole-job throughput of independent replicas (one per rank, the same
+    units each): the slowest rank's time (MAX over ranks) and the units of
+    all ranks divided by it.  Returns (ms_max, units per second)."""
+    import torch
+    ms_max = float(ms_local)
+    if dist is not None:
+        t = torch.tensor([ms_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return ms_max, units_local * world / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -303,13 +316,7 @@ def run_ours(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    total_units = g.cells * args.steps * world
-    value = total_units / (ms_max / 1e3)
+    ms_max, value = aggregate_ranks(ms, g.cells * args.steps, world, dist, dev)
     ms_per_step = ms_max / args.steps
 
     # roofline of the step kernel: 2 algorithmic bytes per compact update
