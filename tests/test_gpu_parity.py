@@ -285,6 +285,22 @@ def test_run_host_matches_device(P):
     assert np.array_equal(hout.numpy(), o.step(init, steps=7))
 
 
+def test_run_host_large_state(P):
+    # 3^17 = 129,140,163 bytes each way (an odd size, larger than L2): the
+    # result must equal the device-resident step, which the oracle checks
+    # elsewhere
+    fam, r = W.TRIANGLE, 17
+    g = gpu_fr(P, fam, r)
+    x = g.init_bernoulli(78, 0.4)
+    want = g.step(x, steps=2).cpu()
+    hin = x.cpu().pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    g.run_host(hin, hout, steps=2)
+    assert torch.equal(hout, want)
+    del x, want
+    torch.cuda.empty_cache()
+
+
 # ---------------------------------------------------- full-size, sampled
 
 def _full_size_check(P, inst, samples, gens=(1, 2)):
