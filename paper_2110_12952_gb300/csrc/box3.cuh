@@ -9,7 +9,10 @@
 // Box layout (host plan): rows of Px bytes (a multiple of 16 with at least
 // one zero word after the last padded cell), Py = B + 2 rows per plane,
 // B + 2 planes; a second box of the same layout right after it holds the
-// totals.  Box offsets of the tile's cells are 16-bit, two per table word.
+// totals.  Box offsets of the tile's cells are 16-bit, two per table word,
+// read from global memory (the same for every tile, so they stay in L1);
+// results go straight to memory.  Without a table or an output stage in
+// shared memory a tile of depth 3 needs 70 KB: three blocks per SM.
 #pragma once
 
 #include <stdint.h>
@@ -87,17 +90,18 @@ __device__ __forceinline__ void box3_rows(const StepArgs &a, const uint8_t *box,
 
 struct Box3Policy {
     static constexpr bool kRingInTile = false;   // halo bytes go to the box
+    static constexpr bool kDirectStore = true;   // no output stage
     struct Regs {};
     __device__ static void init(const StepArgs &, Regs &) {}
     // four consecutive cells per thread: their box offsets in one 8-byte
     // load, their states from two aligned words of the input stage
-    __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *box, const uint32_t *tab, Regs &)
+    __device__ static void scatter(const StepArgs &a, const TileIO &io, uint8_t *box, const uint32_t *, Regs &)
     {
-        const uint16_t *tab16 = reinterpret_cast<const uint16_t *>(tab);
+        const uint2 *tab4 = reinterpret_cast<const uint2 *>(a.tab);   // 4 offsets per entry
         const uint8_t *wp = io.data + (io.a_in & ~3);
         const uint32_t sh = 8u * (uint32_t)(io.a_in & 3);
         for (int64_t l0 = 4 * (int64_t)threadIdx.x; l0 < a.KL; l0 += 4 * (int64_t)blockDim.x) {
-            const uint2 pp = *reinterpret_cast<const uint2 *>(tab16 + l0);
+            const uint2 pp = __ldg(tab4 + l0 / 4);
             const uint32_t p[4] = {pp.x & 0xffffu, pp.x >> 16, pp.y & 0xffffu, pp.y >> 16};
             const uint32_t st = __funnelshift_r(lds32(wp + l0), lds32(wp + l0 + 4), sh);
 #pragma unroll
@@ -105,7 +109,7 @@ struct Box3Policy {
                 if (l0 + i < a.KL) box[p[i]] = ((st >> (8 * i)) & 0xffu) != 0;
         }
     }
-    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *box, const uint32_t *tab,
+    __device__ static void compute(const StepArgs &a, const TileIO &io, const uint8_t *box, const uint32_t *,
                                    Regs &)
     {
         uint8_t *tbox = const_cast<uint8_t *>(box) + a.box_bytes / 2;
@@ -119,16 +123,23 @@ struct Box3Policy {
         // four consecutive cells per thread: their box offsets in one 8-byte
         // load, state and total from the two boxes (the input stage is being
         // refilled by now); a live cell's total counts itself, hence the
-        // survival mask shifted up by one
-        const uint16_t *tab16 = reinterpret_cast<const uint16_t *>(tab);
-        uint8_t *tout = io.ostage + io.a_out;
+        // survival mask shifted up by one.  The four results go to memory as
+        // one word where it is aligned (a warp writes 128 consecutive bytes)
+        const uint2 *tab4 = reinterpret_cast<const uint2 *>(a.tab);
         const uint32_t live = io.rule.survive << 1, dead = io.rule.birth;
         for (int64_t l0 = 4 * (int64_t)threadIdx.x; l0 < a.KL; l0 += 4 * (int64_t)blockDim.x) {
-            const uint2 pp = *reinterpret_cast<const uint2 *>(tab16 + l0);
+            const uint2 pp = __ldg(tab4 + l0 / 4);
             const uint32_t p[4] = {pp.x & 0xffffu, pp.x >> 16, pp.y & 0xffffu, pp.y >> 16};
+            uint32_t w = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (l0 + i < a.KL) tout[l0 + i] = (uint8_t)(((box[p[i]] ? live : dead) >> tbox[p[i]]) & 1u);
+                if (l0 + i < a.KL) w |= (((box[p[i]] ? live : dead) >> tbox[p[i]]) & 1u) << (8 * i);
+            uint8_t *op = io.gout + l0;
+            if (l0 + 4 <= a.KL && ((uintptr_t)op & 3) == 0) {
+                *reinterpret_cast<uint32_t *>(op) = w;
+            } else {
+                for (int i = 0; i < 4 && l0 + i < a.KL; ++i) op[i] = (uint8_t)(w >> (8 * i));
+            }
         }
     }
 };

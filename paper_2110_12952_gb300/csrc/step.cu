@@ -684,7 +684,7 @@ static Geometry plan_geometry(const fractal *f, int L)
             g.Px = Px;
             g.Py = g.B + 2;
             g.planes = g.B + 2;
-            g.tab_entries = (ipow(f->k, L) + 3) / 4 * 2;   // 16-bit box offsets, two per word
+            g.tab_entries = 0;   // its 16-bit box offsets are read from global memory
             g.box_bytes = 2 * round16(vol + 16);            // the box, then the totals box
             return g;
         }
@@ -746,7 +746,8 @@ static Layout plan_layout(const fractal *f, int L)
     y.off_tab = off;
     off += round16(4 * g.tab_entries);
     y.off_out = off;
-    off += (g.data_bytes > 0) ? 0 : kStagePad + y.tile_bytes;   // padded units store straight to memory
+    // padded units and box3 store straight to memory
+    off += (g.data_bytes > 0 || g.mode == kModeBox3) ? 0 : kStagePad + y.tile_bytes;
     y.total = off;
     return y;
 }
@@ -916,7 +917,7 @@ int ensure_step_plan(fractal *f)
             occ[o] = 1;
         }
         if (p.mode == kModeBox3) {
-            tab.assign(geo.tab_entries, 0u);
+            tab.assign((size_t)(p.KL + 3) / 4 * 2, 0u);
             for (int64_t l = 0; l < p.KL; ++l) tab[l / 2] |= pos[l] << (16 * (l % 2));
         } else if (p.mode != kModeCell) {
             // group g = cells [g k^G, (g+1) k^G); its block sits at s^G * (coarse
@@ -1974,6 +1975,17 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
     if (!Pol::kPadded && lane == 0) bulk_wait_all();
 }
 
+// Whether a box policy writes its results straight to memory (io.gout)
+// rather than to the output stage: the policy's kDirectStore, else false.
+template <class Pol, class = void>
+struct DirectStore {
+    static constexpr bool value = false;
+};
+template <class Pol>
+struct DirectStore<Pol, std::void_t<decltype(Pol::kDirectStore)>> {
+    static constexpr bool value = Pol::kDirectStore;
+};
+
 // Tile loop of the policies that compute from the box: wait for the tile's
 // stage; scatter its cells and halo into the box (halo values prefetched
 // into registers during the previous tile when its stage had landed);
@@ -2032,6 +2044,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
         io.ostage = ostage;
         io.a_in = (int)(start - lo);
         io.a_out = (int)(ostart - olo);
+        io.gout = (uint8_t *)ostart;
         tile_rule<MULTI>(a, Tg, io.rule);
 
         Pol::scatter(a, io, box, tab, R);
@@ -2080,7 +2093,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
                 pref = true;
             }
         }
-        if (tid == 0) bulk_wait_read_all();   // previous tile's bulk store has read ostage
+        if (!DirectStore<Pol>::value && tid == 0) bulk_wait_read_all();   // previous tile's bulk store has read ostage
         __syncthreads();
         // stage s is consumed (policies that compute from the stage itself
         // refill it after the compute): refill it with the tile nstage
@@ -2097,6 +2110,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
             fence_proxy_async_smem();
             if (Tn < a.NT) issue_tile(a, resolve<MULTI>(a, in, out, Tn), stage, &bars[s]);
         }
+        if constexpr (DirectStore<Pol>::value) continue;   // the compute wrote the results
         uint8_t *tout = ostage + io.a_out;
         const uintptr_t c0 = (ostart + 15) & ~(uintptr_t)15;
         const uintptr_t c1 = oend & ~(uintptr_t)15;
@@ -2123,7 +2137,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
 }
 
 template <int DIM, int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, MODE == kModeBox3 ? 2 : (MODE == kModeTap || MODE == kModeRows0 || MODE == kModeRows1 || MODE == kModeLid1 ? 3 : 4))
+__global__ void __launch_bounds__(256, MODE == kModeTap || MODE == kModeRows0 || MODE == kModeRows1 || MODE == kModeLid1 || MODE == kModeBox3 ? 3 : 4)
 step_tma_kernel(FracDev F, StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     using Pol = typename PolicyOf<DIM, MODE>::type;
