@@ -70,7 +70,27 @@ FULL_SQUARE = _family("full_square", 2, 2, lambda c: True)
 #: level; for this table the replica ID equals the paper's procedural Eq. 2.
 TRIANGLE_MIRRORED = Family("triangle_mirrored", 3, 2, 2, ((0, 0), (1, 0), (1, 1)))
 
-FAMILIES = {f.name: f for f in (TRIANGLE, CARPET, VICSEK, MENGER, FULL_SQUARE, TRIANGLE_MIRRORED)}
+# Further fractals of Table 1 (Sec. 1).  Their NBB steps are drawn in the
+# paper, and the drawings are not in its source: the H- and X-fractals and the
+# Cantor set have textbook patterns; for the paper's own "custom" fractals the
+# patterns below are readings with the table's k and s.
+#: H-fractal F^{7,3}: the two outer columns and the centre.
+H_FRACTAL = _family("h_fractal", 3, 2, lambda c: c[0] != 1 or c[1] == 1)
+#: X-fractal F^{5,3}: the four corners and the centre.
+X_FRACTAL = _family("x_fractal", 3, 2, lambda c: (c[0] == 1) == (c[1] == 1))
+#: Cantor set F^{2,3}, on a line of the plane: replicas at x = 0 and 2 of row 0.
+CANTOR = _family("cantor_set", 3, 2, lambda c: c[1] == 0 and c[0] != 1)
+#: Chandelier F^{4,3} (reading): the top row and the centre below it.
+CHANDELIER = _family("chandelier", 3, 2, lambda c: c[1] == 0 or c == (1, 1))
+#: Candy F^{12,4} (reading): the 12 border cells of the 4 x 4 box.
+CANDY = _family("candy", 4, 2, lambda c: c[0] in (0, 3) or c[1] in (0, 3))
+#: Empty-Bottles F^{7,3} (reading): the 3 x 3 box without the top two cells of
+#: the middle column, a cup open at the top.
+EMPTY_BOTTLES = _family("empty_bottles", 3, 2, lambda c: not (c[0] == 1 and c[1] < 2))
+
+TABLE1_EXTRA = (H_FRACTAL, X_FRACTAL, CANTOR, CHANDELIER, CANDY, EMPTY_BOTTLES)
+
+FAMILIES = {f.name: f for f in (TRIANGLE, CARPET, VICSEK, MENGER, FULL_SQUARE, TRIANGLE_MIRRORED) + TABLE1_EXTRA}
 
 
 def rule_masks(birth, survive):

@@ -145,6 +145,36 @@ def test_step_exhaustive_all_tile_depths(P, fam, r, levels):
         assert np.array_equal(out.cpu().numpy(), ref), f"L={L}"
 
 
+@pytest.mark.parametrize("fam,r", [(W.H_FRACTAL, 4), (W.X_FRACTAL, 4), (W.CANTOR, 6), (W.CHANDELIER, 5),
+                                   (W.CANDY, 3), (W.EMPTY_BOTTLES, 4)], ids=lambda v: getattr(v, "name", str(v)))
+def test_table1_fractals_every_tile_depth(P, fam, r):
+    # the further Table 1 fractals run through the generic group and cell
+    # policies (s = 3 or 4, k = 2 .. 12): every tile depth, three generations
+    from paper_2110_12952_gb300.capi import FractalError
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(500 + fam.k, 0.5)
+    ref = o.step(init, rule=oracle_rule(fam), steps=3)
+    x = torch.from_numpy(init).cuda()
+    for L in range(0, r + 1):
+        g.tile_levels = L
+        if (fam.s ** L + 2) ** 2 > 100_000:
+            # a sparse fractal's tile box outgrows shared memory: refused
+            with pytest.raises(FractalError, match="does not fit"):
+                g.step(x, steps=3, rule=rule_of(fam))
+            continue
+        out = g.step(x, steps=3, rule=rule_of(fam))
+        assert np.array_equal(out.cpu().numpy(), ref), f"L={L}"
+
+
+@pytest.mark.parametrize("fam,r,L", [(W.H_FRACTAL, 7, 3), (W.CANDY, 6, 3)], ids=lambda v: getattr(v, "name", str(v)))
+def test_table1_fractals_many_tiles(P, fam, r, L):
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    init = o.init_bernoulli(600 + fam.k, 0.4)
+    g.tile_levels = L
+    out = g.step(torch.from_numpy(init).cuda(), steps=2, rule=rule_of(fam))
+    assert np.array_equal(out.cpu().numpy(), o.step(init, rule=oracle_rule(fam), steps=2))
+
+
 @pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 7, 8, 9])
 def test_triangle_many_tiles_per_cta(P, L):
     # r = 14 gives thousands of tiles at every depth, so each CTA reuses its

@@ -61,6 +61,15 @@ def test_carpet_membership_no_centre_digit(r):
     assert np.array_equal(m, np.array(expect, dtype=np.uint8))
 
 
+@pytest.mark.parametrize("r", range(0, 7))
+def test_cantor_set_textbook(r):
+    # the Cantor set: x has no base-3 digit 1, on the row y = 0
+    f = F(W.CANTOR, r)
+    c = all_coords(f.side, 2)
+    expect = [y == 0 and all(d != 1 for d in digits(x, 3, r)) for x, y in c]
+    assert np.array_equal(f.member(c), np.array(expect, dtype=np.uint8))
+
+
 @pytest.mark.parametrize("r", range(0, 4))
 def test_menger_membership_textbook(r):
     f = F(W.MENGER, r)
@@ -74,7 +83,8 @@ def test_menger_membership_textbook(r):
 
 
 @pytest.mark.parametrize("fam,rmax", [(W.TRIANGLE, 8), (W.CARPET, 4), (W.VICSEK, 5),
-                                      (W.MENGER, 3), (W.FULL_SQUARE, 6)])
+                                      (W.MENGER, 3), (W.FULL_SQUARE, 6)] +
+                         [(f, 4) for f in W.TABLE1_EXTRA])
 def test_member_count_is_k_pow_r(fam, rmax):
     # Eq. 1: V = k^r
     for r in range(rmax + 1):
@@ -99,7 +109,9 @@ def test_hausdorff_dimension_table1():
         assert round(math.log(k) / math.log(s), 2) == pytest.approx(v)
     # box-counting dimension of the oracle's fractals equals the table's value
     for fam, name in [(W.TRIANGLE, "sierpinski_gasket"), (W.CARPET, "sierpinski_carpet"),
-                      (W.VICSEK, "vicsek")]:
+                      (W.VICSEK, "vicsek"), (W.H_FRACTAL, "h_fractal"), (W.X_FRACTAL, "x_fractal"),
+                      (W.CANTOR, "cantor_set"), (W.CHANDELIER, "chandelier"), (W.CANDY, "candy"),
+                      (W.EMPTY_BOTTLES, "empty_bottles")]:
         k, s, v = table[name]
         assert (fam.k, fam.s) == (k, s)
         n3 = F(fam, 3).member(all_coords(fam.s ** 3, 2)).sum()
@@ -316,7 +328,8 @@ def test_full_square_random_vs_convolution():
 
 
 @pytest.mark.parametrize("fam,r", [(W.TRIANGLE, 6), (W.CARPET, 3), (W.VICSEK, 4),
-                                   (W.TRIANGLE_MIRRORED, 5), (W.TRIANGLE, 1)])
+                                   (W.TRIANGLE_MIRRORED, 5), (W.TRIANGLE, 1)] +
+                         [(f, 3) for f in W.TABLE1_EXTRA])
 def test_three_routes_agree_2d(fam, r):
     # (i) library convolution on the masked box, (ii) oracle BB step,
     # (iii) oracle compact step through lambda/nu.
