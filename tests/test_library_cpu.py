@@ -77,7 +77,7 @@ def test_workloads_reproducible():
     assert all(10 <= q.instance.steps <= 1000 for q in tr)
 
 
-def test_presets_are_the_survey_tables():
+def test_presets_match_their_offset_tables():
     assert W.TRIANGLE.offsets == ((0, 0), (1, 0), (0, 1))
     assert W.CARPET.k == 8 and (1, 1) not in W.CARPET.offsets
     assert W.VICSEK.offsets == ((1, 0), (0, 1), (1, 1), (2, 1), (1, 2))
