@@ -1416,6 +1416,17 @@ __device__ __forceinline__ void stream_words(const uint32_t *R, uint32_t *S, std
     ((S[W] = stream_word<W>(R)), ...);
 }
 
+// A 1 the compiler cannot see: additions written as a * kOne + b stay
+// integer multiply-adds, which run on the FMA pipe, instead of becoming
+// ALU additions (the ALU pipe, at half rate, is the tap kernel's busiest).
+__constant__ uint32_t kOne = 1u;
+__device__ __forceinline__ uint32_t mad_u32(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 // totals (3x3 sums including the cell) of group J of a unit: lids 0..3 in
 // R[3J], 4..7 in R[3J + 1], lid 8 in byte 2 of R[3J + 2]
 template <int J>
@@ -1432,12 +1443,18 @@ __device__ __forceinline__ void unit_group(const uint32_t *v, const uint32_t *x,
     const uint32_t s1 = tap_byte<tap_src(J, 6)>(v, x), sw4 = tap_byte<tap_src(J, 7)>(v, x);
     // lids 0..3: t0 + N8 + W4 | t0 + l3 + l5 + N8 | t0 + l6 + l7 + W4 | t1 + l1
     // (selector nibble 8: the sign of byte 0 replicated, i.e. 0)
-    R[3 * J] = prmt(P0, P1, 0x6222u) + prmt(A, B, 0x1638u) + prmt(B, 0u, 0x4314u) + w4 * 0x00010001u +
-               n8 * 0x00000101u;
+    // (every addition a multiply-add: see kOne)
+    const uint32_t one = kOne;
+    R[3 * J] = mad_u32(n8, 0x00000101u,
+                       mad_u32(w4, 0x00010001u,
+                               mad_u32(mad_u32(prmt(P0, P1, 0x6222u), one, prmt(A, B, 0x1638u)), one,
+                                       prmt(B, 0u, 0x4314u))));
     // lids 4..7: t1 + NE8 + E0 + E2 | t1 + l1 + l7 | t2 + l2 | t2 + l2 + l5
-    R[3 * J + 1] = prmt(P1, P2, 0x6622u) + prmt(A, 0u, 0x2214u) + prmt(B, 0u, 0x1434u) + (ne8 + e0 + e2);
+    R[3 * J + 1] = mad_u32(mad_u32(mad_u32(prmt(P1, P2, 0x6622u), one, prmt(A, 0u, 0x2214u)), one,
+                                   prmt(B, 0u, 0x1434u)),
+                           one, mad_u32(mad_u32(ne8, one, e0), one, e2));
     // lid 8 (byte 2): t2 + SW4 + S0 + S1
-    R[3 * J + 2] = P2 + ((sw4 + s0 + s1) << 16);
+    R[3 * J + 2] = mad_u32(mad_u32(mad_u32(sw4, one, s0), one, s1), 0x10000u, P2);
 }
 
 // external tap cell C, 0 or 1, read from the stage
