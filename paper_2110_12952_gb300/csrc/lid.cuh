@@ -36,11 +36,21 @@ struct LidTerm {
 };
 
 // totals of unit word W: the sum of its 9 term words (3x3 sums including the
-// cell, <= 9 per byte: no carries)
+// cell, <= 9 per byte: no carries), added as integer multiply-adds by kOne so
+// that the additions issue on the FMA pipe rather than the ALU pipe, which
+// the term words' prmt already keep busy
+template <int P, int U, int W, int D>
+__device__ __forceinline__ void lid_acc(const uint32_t *v, const uint32_t *x, uint32_t &t)
+{
+    if constexpr (D == 0) t = assemble<LidTerm<P, U, W, D>>(v, x, nullptr);
+    else t = mad_u32(assemble<LidTerm<P, U, W, D>>(v, x, nullptr), kOne, t);
+}
 template <int P, int U, int W, int... D>
 __device__ __forceinline__ uint32_t lid_total(const uint32_t *v, const uint32_t *x, std::integer_sequence<int, D...>)
 {
-    return (assemble<LidTerm<P, U, W, D>>(v, x, nullptr) + ...);
+    uint32_t t = 0;
+    (lid_acc<P, U, W, D>(v, x, t), ...);
+    return t;
 }
 
 template <int P, int U, int E>

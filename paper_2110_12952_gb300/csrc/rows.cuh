@@ -212,11 +212,13 @@ __device__ __forceinline__ void unit_band(const uint8_t *tin, const uint32_t *e,
     (band_row<P, Y, RY>(v, x, r), ...);
 #pragma unroll
     for (int y = 3 * Y; y < 3 * Y + 3; ++y) {
-        const uint32_t V0 = r[3 * y] + r[3 * y + 3] + r[3 * y + 6];
-        const uint32_t V1 = r[3 * y + 1] + r[3 * y + 4] + r[3 * y + 7];
-        const uint32_t V2 = r[3 * y + 2] + r[3 * y + 5] + r[3 * y + 8];
-        t[3 * y] = V0 + __funnelshift_r(V0, V1, 8) + __funnelshift_r(V0, V1, 16);
-        t[3 * y + 1] = V1 + __funnelshift_r(V1, V2, 8) + __funnelshift_r(V1, V2, 16);
+        // additions as integer multiply-adds by kOne: the FMA pipe, not the ALU
+        const uint32_t one = kOne;
+        const uint32_t V0 = mad_u32(mad_u32(r[3 * y], one, r[3 * y + 3]), one, r[3 * y + 6]);
+        const uint32_t V1 = mad_u32(mad_u32(r[3 * y + 1], one, r[3 * y + 4]), one, r[3 * y + 7]);
+        const uint32_t V2 = mad_u32(mad_u32(r[3 * y + 2], one, r[3 * y + 5]), one, r[3 * y + 8]);
+        t[3 * y] = mad_u32(mad_u32(V0, one, __funnelshift_r(V0, V1, 8)), one, __funnelshift_r(V0, V1, 16));
+        t[3 * y + 1] = mad_u32(mad_u32(V1, one, __funnelshift_r(V1, V2, 8)), one, __funnelshift_r(V1, V2, 16));
         t[3 * y + 2] = V2 * 0x010101u;
     }
     (band_word<P, Y, I>(rule, v, t, o), ...);
