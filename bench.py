@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-plain-requests", type=int, default=600)
     ap.add_argument("--serve-chunk", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -73,10 +73,26 @@ def measured_peak():
         return 6800.0, "fallback (6.8 TB/s, one earlier GB300 copy measurement)"
 
 
+def kernel_sources(top: str = KERNEL_SRC) -> list:
+    """The step kernel's source and every file it includes with #include "...",
+    followed transitively."""
+    import re
+    seen, todo = [], [os.path.normpath(top)]
+    while todo:
+        path = todo.pop(0)
+        if path in seen or not os.path.exists(path):
+            continue
+        seen.append(path)
+        with open(path) as fh:
+            for m in re.finditer(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), re.M):
+                todo.append(os.path.normpath(os.path.join(os.path.dirname(path), m.group(1))))
+    return seen
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for name in ("step.cu", "step.h", "tma.cuh", "internal.cuh", "handle.h"):
-        with open(os.path.join(ROOT, "paper_2110_12952_gb300", "csrc", name), "rb") as fh:
+    for path in kernel_sources():
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -122,11 +122,12 @@ int fractal_step(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
                  int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
                  void *stream);
 
-/* fractal_step without any device allocation (the paper has no counterpart:
- * this serves callers that must not allocate device memory while they run,
- * such as code being captured into a CUDA graph under a capture mode that
- * forbids cudaMalloc, or applications whose device memory is fixed up
- * front).  Same arguments and results as fractal_step, but:
+/* fractal_step without any device allocation (the paper has no counterpart).
+ * It serves callers that cannot allocate device memory while they run:
+ * applications whose device memory is handed out up front by their own pool
+ * or by another framework that reserves it, and real-time loops in which
+ * cudaMalloc/cudaFree are not acceptable because they may synchronise the
+ * whole device.  Same arguments and results as fractal_step, but:
  *   - the ping-pong buffer for steps > 1 is a fixed 32 MiB device array
  *     inside the library (held on every GPU that loads the library until the
  *     process exits), so k^r must be at most 33,554,432 cells; larger states
@@ -134,9 +135,10 @@ int fractal_step(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
  *   - the handle's tables must already exist: they are built (and
  *     allocated) by the handle's first fractal_step, fractal_autotune or
  *     fractal_get_tile_levels call; otherwise FR_EINVAL;
- *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture;
+ *   - the first call on each device (and the first after that device's
+ *     context changed, e.g. after cudaDeviceReset) looks up the array's
+ *     device address in the current context (cudaGetSymbolAddress) and
+ *     caches it; make that first call before any stream capture;
  *   - the array is shared by every call in the process and keeps the last
  *     call's contents (no call needs it to start at zero: each generation
  *     overwrites it completely before it is read); calls whose work overlaps
@@ -245,9 +247,10 @@ int fractal_batch_stats(const fractal_batch_t *b, int64_t *updates, int64_t *lau
  *   hbm_budget_bytes  admission budget (<= 0: 90% of the free memory now);
  *                     a request needing more than the budget gets FR_EBUSY.
  *   chunk             generations per tick (>= 1).
- * Handles submitted to a server must outlive it and must not be re-planned
- * (fractal_set_tile_levels, fractal_autotune) while it runs; the first submit
- * of a handle builds its tables on the caller's thread. */
+ * Handles submitted to a server must outlive it.  While a server holds a
+ * request of a handle that is not done, fractal_set_tile_levels (with a new
+ * depth) and fractal_autotune on that handle return FR_EBUSY.  The first
+ * submit of a handle builds its tables on the caller's thread. */
 typedef struct fractal_server fractal_server_t;
 int fractal_server_create(int64_t hbm_budget_bytes, int chunk, fractal_server_t **out);
 int fractal_server_destroy(fractal_server_t *srv);   /* finishes all requests first */
@@ -272,6 +275,18 @@ int fractal_sync(void *stream);
  * gave up a bounded device-side wait since the last check (the outputs of
  * that call are then invalid), FR_OK otherwise.  Clears the flag. */
 int fractal_check(fractal_t *f);
+
+/* Failure-detection test hook (not in the paper).  The next compact-step
+ * kernel launch of this handle (the first generation of the next
+ * fractal_step) arms each of its pipeline stages' barriers for extra_bytes
+ * more bytes than it copies, so no stage ever completes, and each of its
+ * bounded waits gives up after wait_tries tries (each try suspends for at
+ * most about a microsecond) instead of the default ~4 million.  The kernel
+ * then records the timeout, waits (bounded) for the copies it issued, and
+ * returns without writing further results: that call's output is invalid and
+ * the next fractal_check returns FR_ETIMEOUT.  Later launches are unaffected.
+ * extra_bytes in [1, 4096], wait_tries in [1, 2^20], else FR_EINVAL. */
+int fractal_test_arm_timeout(fractal_t *f, uint32_t extra_bytes, uint32_t wait_tries);
 
 #ifdef __cplusplus
 }

@@ -65,6 +65,7 @@ SIGNATURES = {
     "fractal_server_wait_all": (c_int, [c_vp]),
     "fractal_server_stats": (c_int, [c_vp, c_i64p, c_i64p, c_i64p, c_i64p, c_i64p, c_i64p]),
     "fractal_autotune": (c_int, [c_fp, c_vp, c_vp, c_u32, c_u32, c_vp, ctypes.POINTER(c_int)]),
+    "fractal_test_arm_timeout": (c_int, [c_fp, c_u32, c_u32]),
 }
 
 

@@ -23,6 +23,8 @@ void set_error(int code, const std::string &msg)
     g_err = msg;
 }
 
+void clear_error() { g_err.clear(); }
+
 int cuda_fail(cudaError_t e, const char *what)
 {
     set_error(FR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -173,6 +175,8 @@ extern "C" int fractal_set_tile_levels(fractal_t *f, int levels)
     if (!f) return fail(FR_EINVAL, "fractal_set_tile_levels: handle is NULL");
     if (levels < -1 || levels > f->r)
         return fail(FR_EINVAL, "fractal_set_tile_levels: levels must be -1 or in [0, r]");
+    if (levels != f->tile_levels_user && f->server_refs.load() > 0)
+        return fail(FR_EBUSY, "fractal_set_tile_levels: a server still holds requests on this handle");
     if (levels != f->tile_levels_user) {
         f->tile_levels_user = levels;
         cudaDeviceSynchronize();
@@ -316,11 +320,25 @@ extern "C" int fractal_check(fractal_t *f)
     return take_status(f);
 }
 
+extern "C" int fractal_test_arm_timeout(fractal_t *f, uint32_t extra_bytes, uint32_t wait_tries)
+{
+    g_err.clear();
+    if (!f) return fail(FR_EINVAL, "fractal_test_arm_timeout: handle is NULL");
+    if (extra_bytes < 1 || extra_bytes > 4096 || wait_tries < 1 || wait_tries > (1u << 20))
+        return fail(FR_EINVAL, "fractal_test_arm_timeout: extra_bytes must be in [1, 4096] and "
+                               "wait_tries in [1, 2^20]");
+    f->test_extra_tx = extra_bytes;
+    f->test_wait_limit = wait_tries;
+    return FR_OK;
+}
+
 extern "C" int fractal_autotune(fractal_t *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                                 uint32_t survive, void *stream, int *levels)
 {
     g_err.clear();
     if (!f || !in || !out) return fail(FR_EINVAL, "fractal_autotune: NULL argument");
     if (overlap(in, out, f->cells)) return fail(FR_EINVAL, "fractal_autotune: in and out overlap");
+    if (f->server_refs.load() > 0)
+        return fail(FR_EBUSY, "fractal_autotune: a server still holds requests on this handle");
     return autotune_step(f, in, out, birth, survive, (cudaStream_t)stream, levels);
 }

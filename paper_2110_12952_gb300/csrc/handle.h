@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -83,6 +84,9 @@ struct fractal {
     uint8_t *bb_scratch = nullptr;   // n^dim bytes, ping-pong for BB steps > 1
     uint8_t *host_io[2] = {nullptr, nullptr};  // device buffers of run_host
     int *status = nullptr;           // device word set by kernels whose bounded waits gave up
+    std::atomic<int> server_refs{0}; // requests of a server not yet done (the plan must not change)
+    uint32_t test_extra_tx = 0;      // fractal_test_arm_timeout: next step launch's extra armed bytes
+    uint32_t test_wait_limit = 0;    // ... and its wait limit (tries)
 };
 
 namespace fr {

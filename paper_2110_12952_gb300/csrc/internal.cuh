@@ -126,6 +126,7 @@ __device__ __forceinline__ int64_t nu_levels(const FracDev &F, uint32_t x, uint3
 // ------------------------------------------------------------ host side
 
 void set_error(int code, const std::string &msg);
+void clear_error();
 int cuda_fail(cudaError_t e, const char *what);
 
 }  // namespace fr

@@ -1,8 +1,9 @@
 // noalloc.cu -- fractal_step_noalloc: the multi-generation compact step
-// without any device allocation, for callers that must not allocate device
-// memory while they run (for example code that is being captured into a
-// CUDA graph with a capture mode that forbids cudaMalloc, or a host
-// application whose memory pool is fixed in advance).
+// without any device allocation, for callers that cannot allocate device
+// memory while they run: applications whose device memory is handed out up
+// front by their own pool or by another framework that reserves it, and
+// real-time loops in which cudaMalloc/cudaFree are not acceptable because
+// they may synchronise the whole device.
 //
 // fractal_step needs a k^r-byte ping-pong buffer when steps > 1 and
 // allocates it on first need.  Here that buffer is the file-scope device
@@ -25,13 +26,47 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
+// The host-side name g_noalloc_scratch is only a stand-in and must never be
+// passed to a kernel.  Its device address belongs to the CUDA context that
+// loaded the module: it is looked up (with the device current) the first
+// time a device is used and again whenever that device's current context is
+// a different one (after cudaDeviceReset, for example, the runtime creates a
+// new primary context and reloads the module, so an older address would
+// dangle).
+struct ScratchAddr {
+    void *ctx = nullptr;
+    uint8_t *ptr = nullptr;
+};
 static std::mutex g_noalloc_mu;
-static uint8_t *g_noalloc_ptr[kMaxDevices];
+static ScratchAddr g_noalloc_addr[kMaxDevices];
 
-// Device address of the array on the current device.  The host-side name
-// g_noalloc_scratch is only a stand-in and must never be passed to a kernel;
-// the address is looked up once per device (with that device current) and
-// cached.
+// cuCtxGetCurrent from the driver, through the runtime's entry-point query
+// (no link-time dependency on libcuda); null if unavailable, in which case
+// the address is looked up on every call.
+using CtxGetCurrent = int (*)(void **);
+static CtxGetCurrent ctx_get_current()
+{
+    static CtxGetCurrent fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetCurrent>(p);
+    }();
+    return fn;
+}
+
+static void *current_ctx()
+{
+    CtxGetCurrent fn = ctx_get_current();
+    void *ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+// Device address of the array in the current context of device `dev`.
 static int noalloc_scratch(int dev, uint8_t **out)
 {
     if (dev < 0 || dev >= kMaxDevices) {
@@ -39,13 +74,18 @@ static int noalloc_scratch(int dev, uint8_t **out)
         return FR_EINVAL;
     }
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "fractal_step_noalloc: cudaGetSymbolAddress");
-        g_noalloc_ptr[dev] = static_cast<uint8_t *>(p);
+    ScratchAddr &c = g_noalloc_addr[dev];
+    void *ctx = current_ctx();
+    if (ctx && c.ctx == ctx && c.ptr) {
+        *out = c.ptr;
+        return FR_OK;
     }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "fractal_step_noalloc: cudaGetSymbolAddress");
+    c.ptr = static_cast<uint8_t *>(p);
+    c.ctx = current_ctx();   // the lookup has made the context current if it was not
+    *out = c.ptr;
     return FR_OK;
 }
 
@@ -56,6 +96,7 @@ using namespace fr;
 extern "C" int fractal_step_noalloc(fractal_t *f, const uint8_t *in, uint8_t *out, int64_t steps,
                                     uint32_t birth, uint32_t survive, void *stream)
 {
+    clear_error();
     if (!f || !in || !out) {
         set_error(FR_EINVAL, "fractal_step_noalloc: NULL argument");
         return FR_EINVAL;

@@ -152,6 +152,7 @@ static void CUDART_CB on_landed(void *arg)
         r->t_done = td;
         if (!r->host_out) r->population = *r->pop_host;
         r->state = kDone;
+        r->f->server_refs.fetch_sub(1);
         s->used -= r->bytes;
         ++s->completed;
         s->gpu_last = td;
@@ -455,6 +456,7 @@ extern "C" int fractal_server_submit(fractal_server_t *s, fractal_t *f, uint64_t
             return FR_EBUSY;
         }
         r->id = s->next_id++;
+        f->server_refs.fetch_add(1);
         s->all[r->id] = r;
         s->queue.push_back(r);
         *id = r->id;
@@ -536,6 +538,7 @@ extern "C" int fractal_server_destroy(fractal_server_t *s)
     cudaStreamSynchronize(s->st);
     for (auto &kv : s->all) {
         Request *r = kv.second;
+        if (r->state != kDone) r->f->server_refs.fetch_sub(1);   // a failed server's leftovers
         if (r->buf[0]) cudaFree(r->buf[0]);
         delete r;
     }

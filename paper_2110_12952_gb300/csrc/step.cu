@@ -74,6 +74,8 @@ struct StepArgs {
     int KG;                // cells per group (group / quad mode)
     int tapz;              // tap mode: index of the all-zero group
     int nq;                // tap mode: units per tile
+    uint32_t wait_limit;   // tries of each bounded wait (kWaitLimit unless a test shortened it)
+    uint32_t extra_tx;     // bytes each stage is armed for beyond its copies (0 unless a test set it)
     const uint32_t *tab;   // cell mode: box offset per cell; else window base per group
     const uint32_t *ring;
     const int32_t *nbr;
@@ -1658,19 +1660,22 @@ __device__ __forceinline__ void issue_tile(const StepArgs &a, const TileRef &t, 
     if (b1 > in_hi) b1 = in_hi;
     const uint32_t row_bytes = 4u * (uint32_t)a.nbrw;
     const uint32_t data_bytes = b1 > b0 ? (uint32_t)(b1 - b0) : 0u;
-    mbar_arrive_expect_tx(bar, row_bytes + data_bytes);
+    mbar_arrive_expect_tx(bar, row_bytes + data_bytes + a.extra_tx);
     bulk_g2s(stage, t.nbr + t.T * a.nbrw, row_bytes, bar);
     if (data_bytes) bulk_g2s(stage + row_bytes + kStagePad + (b0 - lo), (const void *)b0, data_bytes, bar);
 }
 
-// After a failed wait: wait (bounded) for the bulk loads still in flight
-// into this block's stages, those of the block's tiles j0 .. j1 (its
-// iteration numbers), so that no copy lands after the block has exited.
+// After a failed wait: wait (bounded, with the default limit) for the bulk
+// loads still in flight into this block's stages, those of the block's tiles
+// j0 .. j1 (its iteration numbers), so that no copy lands after the block has
+// exited.  Bytes a test armed beyond the copies (extra_tx) are counted as
+// arrived first, so each stage completes exactly when its real copies have.
 __device__ __forceinline__ void drain_loads(const StepArgs &a, uint64_t *bars, int64_t j0, int64_t j1)
 {
     if (threadIdx.x != 0) return;
     for (int64_t j = j0; j <= j1; ++j) {
         if (blockIdx.x + j * (int64_t)gridDim.x >= a.NT) break;
+        if (a.extra_tx) mbar_complete_tx(&bars[j % a.nstage], a.extra_tx);
         mbar_wait_bounded(&bars[j % a.nstage], (uint32_t)((j / a.nstage) & 1));
     }
 }
@@ -1755,14 +1760,14 @@ __device__ __forceinline__ void issue_stage(const StepArgs &a, const TileRef &t,
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive_expect_tx(bar, row_bytes);
+                    mbar_arrive_expect_tx(bar, row_bytes + a.extra_tx);
                     bulk_g2s(stage, nrow, row_bytes, bar);
                 }
             }
             return;
         }
         if (tid == 0) {
-            mbar_arrive_expect_tx(bar, row_bytes + (uint32_t)(a.nq * NB + a.hbytes));
+            mbar_arrive_expect_tx(bar, row_bytes + (uint32_t)(a.nq * NB + a.hbytes) + a.extra_tx);
             bulk_g2s(stage, nrow, row_bytes, bar);
         }
         constexpr int G = Pol::kGroup;
@@ -1886,7 +1891,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         hr.w1 = __ldg(a.ring + 2 * first_halo_run(tid, blockDim.x) + 1);
     }
     TileRef t = resolve<MULTI>(a, in, out, Tg);
-    bool ok = mbar_wait_bounded(&bars[0], 0);
+    bool ok = mbar_wait_bounded(&bars[0], 0, a.wait_limit);
     if (ok) fill_stage<MULTI, Pol>(a, t, smem, filler, rv, false);
     if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
@@ -1970,7 +1975,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
         }
         ok = true;
         if (has_next) {
-            ok = mbar_wait_bounded(&bars[sn], pn);
+            ok = mbar_wait_bounded(&bars[sn], pn, a.wait_limit);
             if (ok) fill_stage<MULTI, Pol>(a, tn, next_stage, filler, rv, pref);
         }
         if (__syncthreads_or(!ok)) {
@@ -2029,7 +2034,7 @@ __device__ __forceinline__ void staged_loop(const StepArgs &a, const uint8_t *in
          Tg += G, ++i, s = (s + 1 == a.nstage) ? 0 : s + 1, parity ^= (s == 0) ? 1u : 0u) {
         uint8_t *stage = smem + s * a.stage_bytes;
         const int32_t *nrow = reinterpret_cast<const int32_t *>(stage);
-        const bool ok = mbar_wait_bounded(&bars[s], parity);
+        const bool ok = mbar_wait_bounded(&bars[s], parity, a.wait_limit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.status, FR_ETIMEOUT);
             drain_loads(a, bars, i, i + a.nstage - 1);
@@ -2262,6 +2267,8 @@ static void fill_args(const fractal *f, StepArgs &a)
     a.KG = p.KG;
     a.tapz = p.tapz;
     a.nq = p.nq;
+    a.wait_limit = kWaitLimit;
+    a.extra_tx = 0;
     a.tab = p.pos;
     a.ring = p.ring;
     a.nbr = p.nbr;
@@ -2312,6 +2319,13 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
     StepArgs a;
     fill_args(f, a);
     make_rule(birth, survive, &a.rule);
+    if (f->test_extra_tx) {
+        // armed by fractal_test_arm_timeout: this launch only
+        a.extra_tx = f->test_extra_tx;
+        a.wait_limit = f->test_wait_limit;
+        f->test_extra_tx = 0;
+        f->test_wait_limit = 0;
+    }
     return dispatch<false>(f, a, f->plan.grid, in, out, st);
 }
 

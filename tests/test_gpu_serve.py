@@ -86,3 +86,28 @@ def test_server_rejects_request_over_budget(P):
     with pytest.raises(FractalError, match="ENOTFOUND"):
         srv.poll(rid + 100)
     srv.close()
+
+
+def test_handle_not_replanned_while_served(P):
+    # a handle with a request still on a server keeps its plan: a new tile
+    # depth and the autotuner are refused until the request is done
+    from paper_2110_12952_gb300.capi import FractalError
+    g = P.Fractal.from_family(W.TRIANGLE, 12)
+    L = g.tile_levels
+    srv = P.Server(hbm_budget_bytes=0, chunk=1)
+    rid = srv.submit(g, 5, 0.4, 400)
+    if not srv.poll(rid)[0]:
+        with pytest.raises(FractalError, match="EBUSY"):
+            g.tile_levels = L - 1
+        x = g.init_bernoulli(1, 0.5)
+        with pytest.raises(FractalError, match="EBUSY"):
+            g.autotune(x, torch.empty_like(x))
+    g.tile_levels = L            # the same depth is always accepted
+    srv.wait_all()
+    assert srv.poll(rid)[0]
+    g.tile_levels = L - 1        # done: re-planning is allowed again
+    assert g.tile_levels == L - 1
+    o = ora(W.TRIANGLE, 12)
+    init = o.init_bernoulli(6, 0.4)
+    assert np.array_equal(g.step(torch.from_numpy(init).cuda(), steps=3).cpu().numpy(), o.step(init, steps=3))
+    srv.close()

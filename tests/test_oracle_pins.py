@@ -259,6 +259,31 @@ def test_nu2d_3d_cycles_axes():
     assert len({tuple(v) for v in c2}) == f.cells
 
 
+def test_nu2d_3d_hand_worked():
+    # reading O6 (axes cycle x, y, z; level mu adds H_mu * k^floor(mu/3) to
+    # axis mu mod 3), worked by hand for the Menger sponge.  Its replica IDs
+    # (row-major, x fastest, tuples with at most one digit 1): (2,0,0) -> 2,
+    # (0,2,1) -> 10, (1,0,2) -> 13, (2,2,2) -> 19, (0,1,0) -> 3, (2,1,2) -> 16.
+    # Levels 0..5 take these tuples in that order, so p = sum_mu 3^mu t_mu:
+    #   x = 2 + 0*3 + 1*9 + 2*27 + 0*81 + 2*243 = 551
+    #   y = 0 + 2*3 + 0*9 + 2*27 + 1*81 + 1*243 = 384
+    #   z = 0 + 1*3 + 2*9 + 2*27 + 0*81 + 2*243 = 561
+    # compact coordinate: x gets 2 (mu 0) + 19*20 (mu 3) = 382, y gets 10
+    # (mu 1) + 3*20 (mu 4) = 70, z gets 13 (mu 2) + 16*20 (mu 5) = 333;
+    # omega = 2 + 10*20 + 13*20^2 + 19*20^3 + 3*20^4 + 16*20^5.
+    tab = {tuple(int(v) for v in row): j for j, row in enumerate(W.MENGER.table())}
+    assert [tab[t] for t in [(2, 0, 0), (0, 2, 1), (1, 0, 2), (2, 2, 2), (0, 1, 0), (2, 1, 2)]] == \
+        [2, 10, 13, 19, 3, 16]
+    f6 = F(W.MENGER, 6)
+    assert f6.nu2d([[551, 384, 561]]).tolist() == [[382, 70, 333]]
+    w = 2 + 10 * 20 + 13 * 400 + 19 * 8000 + 3 * 160000 + 16 * 3200000
+    assert f6.nu([[551, 384, 561]]).tolist() == [w]
+    assert f6.lam([w]).tolist() == [[551, 384, 561]]
+    # the first four levels alone (r = 4): x 65, y 60, z 75 -> (382, 10, 13)
+    f4 = F(W.MENGER, 4)
+    assert f4.nu2d([[65, 60, 75]]).tolist() == [[382, 10, 13]]
+
+
 # ---------------------------------------------------------------- stepping
 
 def life_box(grid, member=None, birth=(3,), survive=(2, 3)):

@@ -1,11 +1,13 @@
 """fractal_step_noalloc, the allocation-free variant of fractal_step, through
 the C ABI.
 
-Callers that cannot allocate device memory while they run (for example code
-being captured into a CUDA graph under a capture mode that forbids cudaMalloc)
-use this entry point; its ping-pong buffer is a fixed device array inside the
-library.  Its results must equal fractal_step's bit for bit, on consecutive
-calls that reuse the shared array.  This file is collected last on purpose.
+Callers that cannot allocate device memory while they run (applications
+whose device memory is handed out up front by their own pool or by another
+framework, real-time loops in which cudaMalloc's possible device-wide
+synchronisation is not acceptable) use this entry point; its ping-pong buffer
+is a fixed device array inside the library.  Its results must equal
+fractal_step's bit for bit, on consecutive calls that reuse the shared array.
+This file is collected last on purpose.
 """
 import ctypes
 
@@ -52,6 +54,34 @@ def test_noalloc_matches_fractal_step_twice(lib):
             assert torch.equal(got, ref), f"{fam.name} r={r} call {call}"
         assert lib.fractal_check(h) == 0
         lib.fractal_destroy(h)
+
+
+def test_noalloc_allocates_nothing(lib):
+    # a handle whose tables were built by fractal_get_tile_levels only (so
+    # fractal_step never allocated its scratch): free device memory is the
+    # same before and after a multi-generation noalloc call, and a failed
+    # call's message does not outlive the next successful call
+    from paper_2110_12952_gb300 import workloads as W
+    stream = torch.cuda.current_stream().cuda_stream
+    h = make_handle(lib, W.TRIANGLE, 12)
+    x = torch.empty(3 ** 12, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    assert lib.fractal_init_bernoulli(h, x.data_ptr(), 3, 0.4, stream) == 0
+    assert lib.fractal_step_noalloc(h, x.data_ptr(), y.data_ptr(), 3, 8, 12, stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert lib.fractal_step_noalloc(h, x.data_ptr(), x.data_ptr(), 3, 8, 12, stream) == -1
+    assert lib.fractal_last_error() != b""
+    assert lib.fractal_step_noalloc(h, x.data_ptr(), y.data_ptr(), 5, 8, 12, stream) == 0
+    assert lib.fractal_last_error() == b""
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ref = torch.empty_like(x)
+    assert lib.fractal_step(h, x.data_ptr(), ref.data_ptr(), 5, 8, 12, stream) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
+    lib.fractal_destroy(h)
 
 
 def test_noalloc_rejects_oversize_and_unprepared(lib):
