@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--serve-chunk", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile-levels", type=int, default=-1, help="tile depth L (-1: library choice)")
+    ap.add_argument("--stages", type=int, default=-1, help="input pipeline stages with --tile-levels (-1: default)")
     return ap.parse_args()
 
 
@@ -298,6 +299,7 @@ def run_ours(args, rank, world, dist):
     b = torch.empty_like(a)
     if args.tile_levels >= 0:
         g.tile_levels = args.tile_levels
+        g.pipeline_stages = args.stages
     else:
         g.autotune(a, b)   # picks the tile depth; untimed
     bufs = [a, b]

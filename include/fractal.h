@@ -179,6 +179,13 @@ int fractal_run_host(fractal_t *f, const uint8_t *host_in, uint8_t *host_out,
 int fractal_set_tile_levels(fractal_t *f, int levels);
 int fractal_get_tile_levels(const fractal_t *f, int *levels);
 
+/* Input pipeline depth of fractal_step: how many tiles each block has in
+ * flight in shared memory (2, 3 or 4), or -1 for the policy's default.  More
+ * stages keep more bytes in flight per block but fit fewer blocks per SM.
+ * Results do not depend on it.  FR_EINVAL outside {-1, 2, 3, 4}; FR_EBUSY
+ * (for a new value) while a server holds requests of the handle. */
+int fractal_set_pipeline_stages(fractal_t *f, int stages);
+
 /* Launch plan of fractal_step for this handle (built, with its
  * allocations, if it does not exist yet, as by fractal_get_tile_levels).
  * info[0..n-1] receives, in order: the policy (0: cell by cell, 3 or 4:
@@ -194,9 +201,10 @@ int fractal_plan_info(const fractal_t *f, int32_t *info, int n);
 
 /* Autotuner of fractal_step: times one generation from in_dev into out_dev
  * (both k^r bytes; out_dev is overwritten) for each candidate tile depth
- * (the deepest whose shared-memory layout fits, and the three below), keeps
- * the fastest for this handle and remembers it for every later handle of the
- * same fractal and level on the same GPU model in this process.  Waits for
+ * (the deepest whose shared-memory layout fits, and the three below) with
+ * 2, 3 and 4 pipeline stages, keeps the fastest plan for this handle and
+ * remembers it for every later handle of the same fractal and level on the
+ * same GPU model in this process.  Waits for
  * `stream`.  *levels (if not NULL) receives the chosen depth. */
 int fractal_autotune(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
                      uint32_t birth_mask, uint32_t survive_mask, void *stream,

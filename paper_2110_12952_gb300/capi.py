@@ -66,6 +66,7 @@ SIGNATURES = {
     "fractal_server_stats": (c_int, [c_vp, c_i64p, c_i64p, c_i64p, c_i64p, c_i64p, c_i64p]),
     "fractal_autotune": (c_int, [c_fp, c_vp, c_vp, c_u32, c_u32, c_vp, ctypes.POINTER(c_int)]),
     "fractal_test_arm_timeout": (c_int, [c_fp, c_u32, c_u32]),
+    "fractal_set_pipeline_stages": (c_int, [c_fp, c_int]),
 }
 
 

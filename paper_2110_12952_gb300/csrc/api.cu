@@ -139,7 +139,7 @@ extern "C" int fractal_create(int k, int s, int r, int dim, const int32_t *offse
         delete f;
         return cuda_fail(e, "fractal_create: no usable CUDA device");
     }
-    f->tile_levels_user = cached_tile_levels(f);
+    f->tile_levels_user = cached_tile_levels(f, &f->stages_user);
     *out = f;
     return FR_OK;
 }
@@ -179,6 +179,22 @@ extern "C" int fractal_set_tile_levels(fractal_t *f, int levels)
         return fail(FR_EBUSY, "fractal_set_tile_levels: a server still holds requests on this handle");
     if (levels != f->tile_levels_user) {
         f->tile_levels_user = levels;
+        cudaDeviceSynchronize();
+        free_step_plan(f->plan);
+    }
+    return FR_OK;
+}
+
+extern "C" int fractal_set_pipeline_stages(fractal_t *f, int stages)
+{
+    g_err.clear();
+    if (!f) return fail(FR_EINVAL, "fractal_set_pipeline_stages: handle is NULL");
+    if (stages != -1 && (stages < 2 || stages > 4))
+        return fail(FR_EINVAL, "fractal_set_pipeline_stages: stages must be -1 or in [2, 4]");
+    if (stages != f->stages_user && f->server_refs.load() > 0)
+        return fail(FR_EBUSY, "fractal_set_pipeline_stages: a server still holds requests on this handle");
+    if (stages != f->stages_user) {
+        f->stages_user = stages;
         cudaDeviceSynchronize();
         free_step_plan(f->plan);
     }

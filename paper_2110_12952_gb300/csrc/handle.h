@@ -78,6 +78,7 @@ struct fractal {
     int device = 0;
     int num_sms = 0;
     int tile_levels_user = -1;
+    int stages_user = -1;            // input pipeline stages (2..4), -1 = the policy's default
     fr::StepPlan plan;
     fr::BBPlan bb;
     uint8_t *scratch = nullptr;      // k^r bytes, ping-pong for steps > 1
@@ -104,7 +105,7 @@ int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, int num_sm
 int preload_copy_kernel();
 int ensure_status(fractal *f);
 int take_status(fractal *f);
-int cached_tile_levels(const fractal *f);
+int cached_tile_levels(const fractal *f, int *stages);
 int autotune_step(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth, uint32_t survive,
                   cudaStream_t st, int *best);
 

@@ -72,7 +72,7 @@ struct StepArgs {
     int off_bar, off_box, off_tab, off_out, box_bytes;
     int ntab;              // entries of the shared table (cells or groups)
     int KG;                // cells per group (group / quad mode)
-    int tapz;              // tap mode: index of the all-zero group
+    int tapz;              // tap mode: byte offset of the all-zero group; unit policies: its index
     int nq;                // tap mode: units per tile
     uint32_t wait_limit;   // tries of each bounded wait (kWaitLimit unless a test shortened it)
     uint32_t extra_tx;     // bytes each stage is armed for beyond its copies (0 unless a test set it)
@@ -190,6 +190,7 @@ constexpr int kExtCells = 14;
 constexpr int kXg[kExtCells] = {0, 1, 2, 3, 4, 5, 5, 6, 7, 8, 9, 10, 11, 11};
 constexpr int kXlid[kExtCells] = {8, 8, 8, 8, 8, 0, 2, 4, 4, 4, 4, 4, 0, 1};
 constexpr int kSrcZero = -1, kSrcBad = -2, kSrcExt = 1000;
+constexpr int kTapHaloGap = 16;   // bytes between a tile's last cell and its first halo group
 
 // Source of tap t of group j of a unit: byte 9 j' + lid of the unit (a
 // group of the same unit), kSrcZero (a hole of the unit's block) or
@@ -233,6 +234,7 @@ static bool is_triangle(const fractal *f)
 // tile-table slot << 24, cell offset in the neighbouring tile).
 struct TapTables {
     int NG = 0, NQ = 0, H = 0;
+    int zero_off = 0;              // byte offset of the all-zero group from the tile's first cell
     std::vector<uint32_t> words;   // NQ * 6
     std::vector<uint32_t> ring;
     bool ok = false;
@@ -348,23 +350,29 @@ static TapTables tap_tables(const fractal *f, int L)
             ext[(size_t)q * kExtGroups + e] = v;
         }
     t.H = (int)slots.size();
-    const int zero = NG + t.H;
-    if (9 * zero + 8 >= 65536) return t;
+    // halo group hs sits kTapHaloGap bytes past the tile's last cell (out of
+    // reach of the tile's 16-byte-rounded bulk copy, so that its plain
+    // stores never race the copy), the zero group after the halo groups
+    auto halo_off = [&](int hs) { return 9 * NG + kTapHaloGap + 9 * hs; };
+    t.zero_off = halo_off(t.H);
+    if (t.zero_off + 8 >= 65536) return t;
     t.words.assign((size_t)t.NQ * kExtGroups / 2, 0);
     for (int q = 0; q < t.NQ; ++q)
         for (int e = 0; e < kExtGroups; ++e) {
             const int v = ext[(size_t)q * kExtGroups + e];
-            const uint32_t g = (v == -2) ? (uint32_t)zero : (v <= -100 ? (uint32_t)(NG + (-100 - v)) : (uint32_t)v);
-            t.words[(size_t)q * (kExtGroups / 2) + e / 2] |= (9u * g) << (16 * (e % 2));
+            const uint32_t b = (v == -2) ? (uint32_t)t.zero_off
+                                         : (v <= -100 ? (uint32_t)halo_off(-100 - v) : 9u * (uint32_t)v);
+            t.words[(size_t)q * (kExtGroups / 2) + e / 2] |= b << (16 * (e % 2));
         }
     // only the halo cells that a tap reads are staged; the other bytes of a
     // halo group are never read
     for (int hs = 0; hs < t.H; ++hs)
         for (int lid = 0; lid < 9; ++lid) {
             if (!((lids_read[hs] >> lid) & 1u)) continue;
-            t.ring.push_back((uint32_t)(9 * (NG + hs) + lid) | ((uint32_t)slots[hs].first << 24));
+            t.ring.push_back((uint32_t)(halo_off(hs) + lid) | ((uint32_t)slots[hs].first << 24));
             t.ring.push_back((uint32_t)(9 * slots[hs].second + lid));
         }
+    if (t.ring.size() / 2 > 32) return t;   // one halo cell per lane of the refilling warp
     t.ok = true;
     return t;
 }
@@ -644,7 +652,7 @@ static Geometry plan_geometry(const fractal *f, int L)
             g.Px = g.Py = g.planes = 0;
             g.tab_entries = 0;   // the unit tables live in registers
             g.halo = t.H;
-            g.halo_bytes = 9 * (t.H + 1);
+            g.halo_bytes = kTapHaloGap + 9 * (t.H + 1);
             g.block = std::max<int64_t>(64, ((int64_t)t.NQ + 31) / 32 * 32);
             g.box_bytes = 0;
             return g;
@@ -734,6 +742,7 @@ static Layout plan_layout(const fractal *f, int L)
     int64_t KL = ipow(f->k, L);
     y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1 ||
                 g.mode == kModeLid1 || g.mode == kModeBox3) ? 2 : nstages();
+    if (f->stages_user >= 2) y.nstage = f->stages_user;
     // slack: 16-byte rounding of the bulk copy, whole-word reads and writes
     // past the tile's last cell; tap mode: halo and zero groups
     y.tile_bytes = round16((g.data_bytes > 0 ? g.data_bytes : KL + g.halo_bytes) + 64);
@@ -749,7 +758,8 @@ static Layout plan_layout(const fractal *f, int L)
     off += round16(4 * g.tab_entries);
     y.off_out = off;
     // padded units and box3 store straight to memory
-    off += (g.data_bytes > 0 || g.mode == kModeBox3) ? 0 : kStagePad + y.tile_bytes;
+    // (warp w's bytes sit 16 w bytes further in, see one_barrier_loop)
+    off += (g.data_bytes > 0 || g.mode == kModeBox3) ? 0 : kStagePad + y.tile_bytes + 16 * ((g.block + 31) / 32);
     y.total = off;
     return y;
 }
@@ -837,7 +847,7 @@ static constexpr uint32_t kZeroSel = 0x8;
 int ensure_step_plan(fractal *f)
 {
     int L = choose_levels(f);
-    if (f->plan.L == L && f->plan.pos) return FR_OK;
+    if (f->plan.L == L && f->plan.pos && f->plan.nstage == (int)plan_layout(f, L).nstage) return FR_OK;
     free_step_plan(f->plan);
     int rc = ensure_status(f);
     if (rc) return rc;
@@ -885,7 +895,7 @@ int ensure_step_plan(fractal *f)
     if (p.mode == kModeTap) {
         const TapTables t = tap_tables(f, L);
         p.KG = 9;
-        p.tapz = t.NG + t.H;
+        p.tapz = t.zero_off;
         p.nq = t.NQ;
         tab = t.words;
         ring = t.ring;
@@ -1497,7 +1507,7 @@ struct TapPolicy {
     // tile's first cell in the stage
     __device__ static void fill(const StepArgs &a, uint8_t *tin, int lane)
     {
-        if (lane < 9) tin[9 * a.tapz + lane] = 0;
+        if (lane < 9) tin[a.tapz + lane] = 0;
     }
     // the tile bytes warp w writes: those of units 32w .. 32w + 31
     __device__ static void warp_bytes(const StepArgs &a, int w, int *b0, int *b1)
@@ -1518,6 +1528,7 @@ struct TapPolicy {
         const uint32_t sh = (uint32_t)(off & 3) * 8u;
         // the unit's 81 cells (bytes 81..83 of v belong to whoever follows)
         uint32_t v[NW];
+        uint32_t x[kExtCells];
         {
             uint32_t w[NW + 1];
 #pragma unroll
@@ -1532,9 +1543,8 @@ struct TapPolicy {
 #pragma unroll
                 for (int i = 0; i < NW; ++i) v[i] = bytes_to_01(v[i]);
             }
+            ext_taps(tin, R.e, x, std::make_integer_sequence<int, kExtCells>());
         }
-        uint32_t x[kExtCells];
-        ext_taps(tin, R.e, x, std::make_integer_sequence<int, kExtCells>());
         uint32_t T[3 * kUnitGroups];
         unit_group<0>(v, x, T);
         unit_group<1>(v, x, T);
@@ -1864,7 +1874,9 @@ __device__ __forceinline__ void fill_stage(const StepArgs &a, const TileRef &t, 
 // one block barrier per tile.  After computing tile i, each warp stores its
 // own bytes of the output stage (a bulk copy of their 16-byte aligned part,
 // plain stores for the ends) and waits for that copy to have read them
-// before it writes the output stage again; every thread waits for tile
+// before it writes the output stage again.  Tile byte j of warp w sits at
+// 16 w + (the tile's output address mod 16) + j, so that a warp's bytes of
+// one tile never overlap another warp's bytes of another tile; every thread waits for tile
 // i+1's stage and fills its share of it, and the barrier that follows both
 // closes tile i and opens tile i+1.  After it, thread 0 refills tile i's
 // input stage.
@@ -1876,7 +1888,7 @@ __device__ __forceinline__ void one_barrier_loop(const StepArgs &a, const uint8_
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool filler = warp == (int)(blockDim.x >> 5) - 1;
     const int64_t G = gridDim.x;
-    uint8_t *ostage = smem + a.off_out + kStagePad;
+    uint8_t *ostage = smem + a.off_out + kStagePad + 16 * warp;   // this warp's view
     int wb0, wb1;   // this warp's bytes of a tile
     Pol::warp_bytes(a, warp, &wb0, &wb1);
     int64_t Tg = blockIdx.x;
@@ -2349,7 +2361,7 @@ int launch_step_multi(const fractal *cls, const InstDesc *descs, const int32_t *
 // ---------------------------------------------------------------- autotune
 
 static std::mutex g_tune_mu;
-static std::map<std::string, int> g_tune_cache;  // fractal + device -> tile levels
+static std::map<std::string, std::pair<int, int>> g_tune_cache;  // fractal + device -> (tile levels, stages)
 
 static std::string tune_key(const fractal *f)
 {
@@ -2362,57 +2374,67 @@ static std::string tune_key(const fractal *f)
     return key;
 }
 
-int cached_tile_levels(const fractal *f)
+int cached_tile_levels(const fractal *f, int *stages)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(tune_key(f));
-    return it == g_tune_cache.end() ? -1 : it->second;
+    if (stages) *stages = it == g_tune_cache.end() ? -1 : it->second.second;
+    return it == g_tune_cache.end() ? -1 : it->second.first;
 }
 
-// Times the candidate tile depths (the deepest that fit in shared memory and
-// the three below) on the caller's buffers and keeps the fastest.
+// Times the candidate plans on the caller's buffers and keeps the fastest:
+// the tile depths (the deepest that fit in shared memory and the three
+// below), each with 2, 3 and 4 input pipeline stages.
 int autotune_step(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth, uint32_t survive,
                   cudaStream_t st, int *best_out)
 {
     int lmax = 0;
+    f->stages_user = -1;
     for (int L = 0; L <= f->r; ++L) {
         if (plan_layout(f, L).total > 200 * 1024) break;
         lmax = L;
     }
-    int best = -1;
+    int best = -1, best_st = -1;
     float best_ms = 0.f;
     cudaEvent_t e0, e1;
     FR_CUDA(cudaEventCreate(&e0));
     FR_CUDA(cudaEventCreate(&e1));
     for (int L = lmax; L >= 0 && L >= lmax - 3; --L) {
         if (ipow(f->k, f->r - L) >= ((int64_t)1 << 31)) break;
-        f->tile_levels_user = L;
-        if (ensure_step_plan(f) != FR_OK) continue;
-        int rc = FR_OK;
-        for (int w = 0; w < 2 && !rc; ++w) rc = launch_step_once(f, in, out, birth, survive, st);
-        if (!rc) rc = (cudaEventRecord(e0, st) == cudaSuccess) ? FR_OK : FR_ECUDA;
-        for (int w = 0; w < 3 && !rc; ++w) rc = launch_step_once(f, in, out, birth, survive, st);
-        if (!rc) rc = (cudaEventRecord(e1, st) == cudaSuccess) ? FR_OK : FR_ECUDA;
-        if (!rc) rc = (cudaEventSynchronize(e1) == cudaSuccess) ? FR_OK : FR_ECUDA;
-        float ms = 0.f;
-        if (!rc && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best < 0 || ms < best_ms)) {
-            best = L;
-            best_ms = ms;
+        for (int ns = 2; ns <= 4; ++ns) {
+            f->tile_levels_user = L;
+            f->stages_user = ns;
+            if (plan_layout(f, L).total > 200 * 1024) continue;
+            if (ensure_step_plan(f) != FR_OK) continue;
+            int rc = FR_OK;
+            for (int w = 0; w < 2 && !rc; ++w) rc = launch_step_once(f, in, out, birth, survive, st);
+            if (!rc) rc = (cudaEventRecord(e0, st) == cudaSuccess) ? FR_OK : FR_ECUDA;
+            for (int w = 0; w < 3 && !rc; ++w) rc = launch_step_once(f, in, out, birth, survive, st);
+            if (!rc) rc = (cudaEventRecord(e1, st) == cudaSuccess) ? FR_OK : FR_ECUDA;
+            if (!rc) rc = (cudaEventSynchronize(e1) == cudaSuccess) ? FR_OK : FR_ECUDA;
+            float ms = 0.f;
+            if (!rc && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best < 0 || ms < best_ms)) {
+                best = L;
+                best_st = ns;
+                best_ms = ms;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best < 0) {
         f->tile_levels_user = -1;
+        f->stages_user = -1;
         set_error(FR_EINVAL, "fractal_autotune: no tile depth could be planned");
         return FR_EINVAL;
     }
     f->tile_levels_user = best;
+    f->stages_user = best_st;
     int rc = ensure_step_plan(f);
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[tune_key(f)] = best;
+        g_tune_cache[tune_key(f)] = std::make_pair(best, best_st);
     }
     if (best_out) *best_out = best;
     return take_status(f);

@@ -156,6 +156,15 @@ class Fractal:
     def tile_levels(self, levels: int):
         self._check(self._lib.fractal_set_tile_levels(self._h, int(levels)))
 
+    @property
+    def pipeline_stages(self) -> int:
+        """Input pipeline stages of the step's plan (``fractal_plan_info``)."""
+        return self.plan_info()["stages"]
+
+    @pipeline_stages.setter
+    def pipeline_stages(self, stages: int):
+        self._check(self._lib.fractal_set_pipeline_stages(self._h, int(stages)))
+
     POLICIES = {0: "cell", 3: "group3", 4: "group4", 9: "quad", 10: "tap", 11: "rows_carpet", 12: "rows_vicsek", 13: "lid_vicsek", 14: "box3"}
 
     def plan_info(self) -> dict:

@@ -130,10 +130,10 @@ def test_triangle_r20_whole_ranges_bench_plan(P):
     torch.cuda.synchronize()
     n = 3 ** 16
     tile = 3 ** g.tile_levels
-    starts = [0, cells // 2 - n // 2, cells - n, 7 * n + 5 * tile - n // 3]
+    starts = [0, cells // 2 - n // 2, cells - n, 7 * n + 5 * tile + 4321]
     ref = np.zeros(cells, dtype=np.uint8)
+    assert starts[3] % tile != 0     # this one starts inside a tile
     for w0 in starts:
-        assert w0 % tile != 0 or w0 == 0
         o.step_range(init, w0, w0 + n, out=ref)
         got = b[w0:w0 + n].cpu().numpy()
         assert np.array_equal(got, ref[w0:w0 + n]), f"range starting at {w0}"

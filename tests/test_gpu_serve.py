@@ -94,6 +94,7 @@ def test_handle_not_replanned_while_served(P):
     from paper_2110_12952_gb300.capi import FractalError
     g = P.Fractal.from_family(W.TRIANGLE, 12)
     L = g.tile_levels
+    g.tile_levels = L            # an explicit depth (the automatic choice is -1)
     srv = P.Server(hbm_budget_bytes=0, chunk=1)
     rid = srv.submit(g, 5, 0.4, 400)
     if not srv.poll(rid)[0]:
