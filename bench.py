@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile-levels", type=int, default=-1, help="tile depth L (-1: library choice)")
     ap.add_argument("--stages", type=int, default=-1, help="input pipeline stages with --tile-levels (-1: default)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1 GPUs: one independent instance per GPU instead of one instance sharded")
+    ap.add_argument("--shard", action="store_true", help="run the sharded path even on one GPU")
+    ap.add_argument("--shard-tile-levels", type=int, default=9, help="tile depth of the sharded instance")
     return ap.parse_args()
 
 
@@ -396,6 +400,103 @@ def run_ours(args, rank, world, dist):
     return line
 
 
+def run_sharded(args, rank, world, dist):
+    """One triangle instance of level --r split over the N ranks (one shard
+    per GPU, contiguous tile ranges): each generation every rank gathers the
+    tiles its peers need, exchanges them with NCCL send/recv straight into the
+    peers' halo regions, and steps its own tiles.  Strong scaling: the
+    instance is the same at every N."""
+    import torch
+    from paper_2110_12952_gb300 import Fractal, build, workloads as W
+    from paper_2110_12952_gb300.shard import ShardPlan, exchange_dist
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    inst = W.TRI_R20 if args.r == 20 else W.Instance(W.TRIANGLE, args.r, 0.3, 3, 1000)
+    fam, L = inst.family, args.shard_tile_levels
+    g = Fractal.from_family(fam, inst.r)
+    plan = ShardPlan.from_family(fam, inst.r, L, world, rank)
+    plan.attach(g)
+    a = torch.zeros(plan.buffer_cells, dtype=torch.uint8, device=dev)
+    full = g.init_bernoulli(inst.seed, inst.p)         # the same instance on every rank
+    a[: plan.local_cells].copy_(full[plan.first_cell: plan.first_cell + plan.local_cells])
+    del full
+    torch.cuda.empty_cache()
+    b = torch.zeros_like(a)
+    bufs = [a, b]
+    cur = [0]
+    peers_with_data = sum(1 for q in range(world) if q != rank and len(plan.sends(q)[0]))
+    halo_bytes = plan.buffer_cells - plan.local_cells
+
+    def one_generation():
+        exchange_dist(plan, bufs[cur[0]], dist)
+        plan.step(bufs[cur[0]], bufs[1 - cur[0]])
+        cur[0] ^= 1
+
+    with ClockSampler(dev.index) as clocks:
+        for _ in range(args.warmup):
+            one_generation()
+        torch.cuda.synchronize()
+        clocks.wait_ready()
+        dist.barrier()
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        t_start = time.monotonic()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one_generation()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_end = time.monotonic()
+    clocks.window(t_start, t_end)
+    dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    cells = fam.k ** inst.r
+    value = cells * args.steps / (ms_max / 1e3)
+    # end to end: the rank's own cells from pinned host memory, one
+    # generation (exchange + step), its own cells back, every step
+    hin = torch.empty(plan.local_cells, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(plan.local_cells, dtype=torch.uint8).pin_memory()
+    hin.copy_(bufs[cur[0]][: plan.local_cells])
+    e2e_steps = max(1, min(args.steps, 5))
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bufs[cur[0]][: plan.local_cells].copy_(hin, non_blocking=True)
+        one_generation()
+        hout.copy_(bufs[cur[0]][: plan.local_cells], non_blocking=True)
+        torch.cuda.synchronize()
+    dt = torch.tensor([(time.perf_counter() - t0) / e2e_steps], dtype=torch.float64, device=dev)
+    dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+    e2e = {"value": cells / float(dt.item()), "unit": UNIT, "h2d_bytes_per_step": plan.local_cells,
+           "d2h_bytes_per_step": plan.local_cells, "ms_per_step": float(dt.item()) * 1e3,
+           "call": "per rank: own cells H2D, halo exchange + fractal_shard_step, own cells D2H, sync",
+           "bytes_note": "per rank; every rank moves its own cells"}
+    peak, peak_src = measured_peak()
+    per_rank_alg = 2.0 * plan.local_cells
+    achieved = per_rank_alg / (ms / args.steps / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": dict(workload_config(inst), parallelism=f"shards{world}", tile_levels=L,
+                           halo_bytes_per_rank=halo_bytes, own_cells_rank0=plan.local_cells),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "step_tma_kernel<2,10,false> over the shard's tiles (rank 0) plus its halo gathers",
+                         "algorithmic_bytes_per_launch": per_rank_alg, "peak_source": peak_src},
+            "gpu_launches": args.steps * (1 + peers_with_data), "e2e": e2e}
+    line["clocks"] = clocks.summary()
+    plan.close()
+    g.close()
+    return line
+
+
 def bb_compare(args, W):
     import torch
     from paper_2110_12952_gb300 import Fractal
@@ -627,13 +728,22 @@ def main():
         if line is not None:
             print(json.dumps(line), flush=True)
         return
-    if world > 1:
+    sharded = args.shard or (world > 1 and not args.replicas)
+    if world > 1 or sharded:
         import torch
         import torch.distributed as tdist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        if world == 1:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29533")
+            os.environ.setdefault("RANK", "0")
+            os.environ.setdefault("WORLD_SIZE", "1")
         tdist.init_process_group("nccl")
         dist = tdist
-    line = run_ours(args, rank, world, dist)
+    if sharded:
+        line = run_sharded(args, rank, world, dist)
+    else:
+        line = run_ours(args, rank, world, dist)
     if rank == 0:
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(args.r, args.cpu_seconds, 3, 0.3)

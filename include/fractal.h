@@ -284,6 +284,65 @@ int fractal_sync(void *stream);
  * that call are then invalid), FR_OK otherwise.  Clears the flag. */
 int fractal_check(fractal_t *f);
 
+/* ---- One instance split over several shards (one per GPU) -------------
+ * The paper's fractal is k replicas of the level below, each a contiguous
+ * omega range filling its own sub-box (Sec. 1, Sec. 3), so an instance
+ * splits into contiguous ranges of tiles (level-L subtrees of k^L cells):
+ * shard g of G owns tiles [floor(g NT / G), floor((g+1) NT / G)), NT =
+ * k^(r-L).  Each generation a shard needs, besides its own tiles, the
+ * neighbouring tiles of other shards that its tiles' Moore neighbourhoods
+ * reach (its halo).  A shard's buffer holds its own tiles (tile t0 + i at
+ * cell i k^L), then its halo tiles grouped by owning shard in increasing
+ * shard order, each group in increasing tile order.  One generation is:
+ * every shard gathers, for each peer, the tiles that peer needs
+ * (fractal_shard_pack) and the caller moves that send buffer into the
+ * peer's buffer at the offset fractal_shard_sends reports (NCCL send/recv,
+ * a peer copy, or a device copy when shards share a GPU); then every shard
+ * runs fractal_shard_step.  Results equal fractal_step on the whole state.
+ *
+ * fractal_shard_plan computes the plan on the host (no GPU needed): the
+ * fractal (as in fractal_create), the tile depth L in [0, r], the number of
+ * shards G >= 1 and this shard's index.  FR_EINVAL for bad arguments or
+ * fewer tiles than shards, FR_EOVERFLOW when NT (3^dim - 1) > 2^28. */
+typedef struct fractal_shard fractal_shard_t;
+int fractal_shard_plan(int k, int s, int r, int dim, const int32_t *offsets, int tile_levels,
+                       int nshards, int shard, fractal_shard_t **out);
+int fractal_shard_destroy(fractal_shard_t *p);
+/* first_cell: omega of the shard's first own cell; local_cells: its own
+ * cells; buffer_cells: own + halo cells (the size of its state buffers). */
+int fractal_shard_info(const fractal_shard_t *p, int64_t *first_cell, int64_t *local_cells,
+                       int64_t *buffer_cells);
+/* The tiles (global tile indices, increasing) this shard sends to `peer`
+ * each generation (tiles may be NULL to query *count; else capacity >=
+ * *count), and *dst_cell, where that block starts in the peer's buffer.
+ * The block is count * k^L bytes, tile after tile. */
+int fractal_shard_sends(const fractal_shard_t *p, int peer, int64_t *tiles, int64_t capacity,
+                        int64_t *count, int64_t *dst_cell);
+/* The tiles this shard receives from `peer` and where they start in this
+ * shard's buffer. */
+int fractal_shard_recvs(const fractal_shard_t *p, int peer, int64_t *tiles, int64_t capacity,
+                        int64_t *count, int64_t *dst_cell);
+/* Host copy of the shard's neighbour table: for own tile i and Moore
+ * direction d (dx, dy[, dz] in -1..1 with x fastest, the centre skipped),
+ * table[i (3^dim - 1) + d] = the tile slot of the shard's buffer that holds
+ * that neighbour (own tiles first, then the halo), or -1 if there is none. */
+int fractal_shard_neighbours(const fractal_shard_t *p, int32_t *table, int64_t capacity);
+/* Binds the plan to a handle of the same fractal on the current device: sets
+ * the handle's tile depth to the plan's and uploads the shard's tables
+ * (device allocations owned by the plan). */
+int fractal_shard_attach(fractal_shard_t *p, fractal_t *f);
+/* Gathers into send_dev (count * k^L bytes, see fractal_shard_sends) the
+ * tiles `peer` needs, read from this shard's buffer_dev.  Asynchronous on
+ * `stream`. */
+int fractal_shard_pack(const fractal_shard_t *p, int peer, const uint8_t *buffer_dev,
+                       uint8_t *send_dev, void *stream);
+/* One generation (Sec. 3 stencil procedure) of the shard's own tiles:
+ * in_dev is a full shard buffer (own tiles and a filled halo), out_dev a
+ * buffer of the same size that does not overlap it; only its own-tile part
+ * is written.  Asynchronous on `stream`. */
+int fractal_shard_step(fractal_shard_t *p, const uint8_t *in_dev, uint8_t *out_dev,
+                       uint32_t birth_mask, uint32_t survive_mask, void *stream);
+
 /* Failure-detection test hook (not in the paper).  The next compact-step
  * kernel launch of this handle (the first generation of the next
  * fractal_step) arms each of its pipeline stages' barriers for extra_bytes

@@ -99,6 +99,11 @@ void free_bb_plan(BBPlan &p);
 
 int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                      uint32_t survive, cudaStream_t st);
+// One generation of the tiles 0 .. ntiles-1 of the buffer `in` (tile T at
+// cell T k^L) with the neighbour table `nbr` (ntiles rows, indices of tiles
+// of the same buffer, which holds readable_cells cells), into `out`.
+int launch_step_tiles(fractal *f, const uint8_t *in, uint8_t *out, const int32_t *nbr, int64_t ntiles,
+                      int64_t readable_cells, uint32_t birth, uint32_t survive, cudaStream_t st);
 int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                    uint32_t survive, cudaStream_t st);
 int launch_copy_normalise(const uint8_t *in, uint8_t *out, int64_t n, int num_sms, cudaStream_t st);

@@ -2341,6 +2341,20 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
     return dispatch<false>(f, a, f->plan.grid, in, out, st);
 }
 
+int launch_step_tiles(fractal *f, const uint8_t *in, uint8_t *out, const int32_t *nbr, int64_t ntiles,
+                      int64_t readable_cells, uint32_t birth, uint32_t survive, cudaStream_t st)
+{
+    if (ntiles <= 0) return FR_OK;
+    StepArgs a;
+    fill_args(f, a);
+    make_rule(birth, survive, &a.rule);
+    a.NT = ntiles;
+    a.cells = readable_cells;
+    a.nbr = nbr;
+    const int grid = (int)std::min<int64_t>((int64_t)f->plan.per_sm * f->num_sms, ntiles);
+    return dispatch<false>(f, a, grid, in, out, st);
+}
+
 int launch_step_multi(const fractal *cls, const InstDesc *descs, const int32_t *tile_inst,
                       int ninst, int64_t total, int gen, cudaStream_t st)
 {
