@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-others", action="store_true")
+    ap.add_argument("--no-maps", action="store_true")
+    ap.add_argument("--maps-only", action="store_true", help="run the maps leg alone and print it")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-plain-requests", type=int, default=600)
@@ -375,6 +377,9 @@ def run_ours(args, rank, world, dist):
     g.close()
     torch.cuda.empty_cache()
 
+    # the maps alone, CUDA cores vs tensor cores
+    if not args.no_maps and rank == 0:
+        extra["maps"] = maps_compare(args, W)
     # compact vs bounding box at equal r
     if not args.no_bb and rank == 0:
         extra["bb_compare"] = bb_compare(args, W)
@@ -495,6 +500,38 @@ def run_sharded(args, rank, world, dist):
     plan.close()
     g.close()
     return line
+
+
+def maps_compare(args, W):
+    """The maps alone (the batch API): lambda of 2^25 seeded compact indices
+    of the triangle at r = 20 and nu / compact coordinate of their
+    coordinates, on the CUDA cores (fractal_lambda, fractal_nu + fractal_nu2d)
+    and with the level sums on the tensor cores (fractal_lambda_tc,
+    fractal_nu_tc).  Inputs are resident; the median of 10 timed calls each."""
+    import torch
+    from paper_2110_12952_gb300 import Fractal
+    g = Fractal.from_family(W.TRIANGLE, 20)
+    n = 1 << 25
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    w = torch.randint(0, g.cells, (n,), dtype=torch.int64, device="cuda", generator=gen)
+    c = g.lam(w)
+    out = {}
+    for name, fn in (("lambda_cuda_core", lambda: g.lam(w, out=c)),
+                     ("lambda_tensor_core", lambda: g.lam_tc(w, out=c)),
+                     ("nu_and_compact_cuda_core", lambda: (g.nu(c), g.nu2d(c))),
+                     ("nu_and_compact_tensor_core", lambda: g.nu_tc(c, compact=True))):
+        ms = statistics.median(time_steps(fn, 10, 3))
+        out[name] = {"ms": ms, "maps_per_s": n / (ms / 1e3)}
+    same = torch.equal(g.lam_tc(w), g.lam(w))
+    om, c2 = g.nu_tc(c, compact=True)
+    same = same and torch.equal(om, g.nu(c)) and torch.equal(c2, g.nu2d(c))
+    out["workload"] = "triangle r=20, 2^25 uniform compact indices (seed 11) and their coordinates"
+    out["tensor_core_equals_cuda_core"] = bool(same)
+    del w, c
+    g.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def bb_compare(args, W):
@@ -730,6 +767,12 @@ def main():
         line = run_reference(args, rank, world)
         if line is not None:
             print(json.dumps(line), flush=True)
+        return
+    if args.maps_only:
+        import torch
+        from paper_2110_12952_gb300 import build, workloads as W
+        build.build()
+        print(json.dumps({"maps": maps_compare(args, W)}), flush=True)
         return
     sharded = args.shard or (world > 1 and not args.replicas)
     if world > 1 or sharded:

@@ -104,6 +104,21 @@ int fractal_nu(const fractal_t *f, const int32_t *coords_dev, int64_t count,
 int fractal_nu2d(const fractal_t *f, const int32_t *coords_dev, int64_t count,
                  int64_t *compact_dev, void *stream);
 
+/* The same maps with their sums over levels on the tensor cores (Sec. 3.1,
+ * the tensor-core encoding of nu, made exact): per warp, 32 cells' replica
+ * IDs (nu) or digit offsets (lambda) form a matrix A, the level weights
+ * (k^mu, tau(k, mu), s^mu) split into 11-bit limbs form B, and
+ * mma.sync.m16n8k16 with fp16 operands and fp32 accumulators computes A B;
+ * every partial sum stays below 2^24, so the results equal fractal_nu /
+ * fractal_nu2d / fractal_lambda exactly.  fractal_nu_tc writes nu to
+ * omega_dev and, if compact_dev is not NULL, the compact coordinate of
+ * fractal_nu2d to compact_dev (count*dim entries).  Limits: r <= 32 and
+ * k <= 255 (nu), dim*r <= 64 (lambda), else FR_EINVAL. */
+int fractal_nu_tc(const fractal_t *f, const int32_t *coords_dev, int64_t count,
+                  int64_t *omega_dev, int64_t *compact_dev, void *stream);
+int fractal_lambda_tc(const fractal_t *f, const int64_t *omega_dev, int64_t count,
+                      int32_t *coords_dev, void *stream);
+
 /* Seeded Bernoulli(p) compact state (not from the paper; synthetic input):
  * state_dev[omega] = 1 iff the top 53 bits of the omega-th SplitMix64 output
  * for `seed` (mix(seed + (omega+1)*0x9e3779b97f4a7c15)) are below

@@ -87,6 +87,25 @@ class Fractal:
                                          _dev_ptr(out, torch.int64, "omega"), _stream(stream)))
         return out
 
+    def lam_tc(self, omega: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """``fractal_lambda_tc``: lambda with its level sums on the tensor cores."""
+        n = omega.numel()
+        out = out if out is not None else torch.empty((n, self.dim), dtype=torch.int32, device=omega.device)
+        self._check(self._lib.fractal_lambda_tc(self._h, _dev_ptr(omega, torch.int64, "omega"), n,
+                                                _dev_ptr(out, torch.int32, "coords"), _stream(stream)))
+        return out
+
+    def nu_tc(self, coords: torch.Tensor, compact: bool = False, stream=None):
+        """``fractal_nu_tc``: nu (and, with ``compact``, the compact coordinate of
+        ``nu2d``) with the level sums on the tensor cores."""
+        n = coords.shape[0]
+        om = torch.empty(n, dtype=torch.int64, device=coords.device)
+        c2 = torch.empty((n, self.dim), dtype=torch.int64, device=coords.device) if compact else None
+        self._check(self._lib.fractal_nu_tc(self._h, _dev_ptr(coords, torch.int32, "coords"), n,
+                                            om.data_ptr(), c2.data_ptr() if c2 is not None else None,
+                                            _stream(stream)))
+        return (om, c2) if compact else om
+
     def nu2d(self, coords: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         n = coords.numel() // self.dim
         out = out if out is not None else torch.empty((n, self.dim), dtype=torch.int64, device=coords.device)
