@@ -201,6 +201,21 @@ int fractal_get_tile_levels(const fractal_t *f, int *levels);
  * (for a new value) while a server holds requests of the handle. */
 int fractal_set_pipeline_stages(fractal_t *f, int stages);
 
+/* Temporal blocking of fractal_step (and fractal_run_host): with
+ * generations = g in [1, 9], every pass over the state advances it by up to
+ * g generations (ceil(steps / g) passes), instead of one.  Each tile (a
+ * level-L subtree) and the level-2 units of its neighbouring tiles that
+ * touch it are loaded once, advanced in shared memory as a bitmap of the
+ * embedded box with one bit per cell (a cell at distance d from the loaded
+ * region's edge is exact for d generations; the tile's cells are 9 or more
+ * cells in), and written back: HBM bytes per cell-update fall from 2 to
+ * about (2 + halo) / g.  Results are those of single generations exactly.
+ * Only for the Sierpinski carpet and the Vicsek fractal with the preset
+ * offset tables (FR_EINVAL otherwise).  tile_levels: -1 = the deepest tile
+ * whose shared memory stays within 100 KB, else in [2, r].  generations = 0
+ * turns it off.  The batch, server and no-allocation calls are unaffected. */
+int fractal_set_temporal_blocking(fractal_t *f, int generations, int tile_levels);
+
 /* Launch plan of fractal_step for this handle (built, with its
  * allocations, if it does not exist yet, as by fractal_get_tile_levels).
  * info[0..n-1] receives, in order: the policy (0: cell by cell, 3 or 4:

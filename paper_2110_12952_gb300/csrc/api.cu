@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -150,6 +151,7 @@ extern "C" int fractal_destroy(fractal_t *f)
     if (!f) return FR_OK;
     cudaDeviceSynchronize();
     free_step_plan(f->plan);
+    free_tb_plan(f->tb);
     free_bb_plan(f->bb);
     cudaFree(f->scratch);
     cudaFree(f->bb_scratch);
@@ -266,6 +268,28 @@ extern "C" int fractal_step(fractal_t *f, const uint8_t *in, uint8_t *out, int64
     if (overlap(in, out, f->cells)) return fail(FR_EINVAL, "fractal_step: in and out overlap");
     cudaStream_t st = (cudaStream_t)stream;
     if (steps == 0) return launch_copy_normalise(in, out, f->cells, f->num_sms, st);
+    if (f->tb_gens > 0) {
+        // temporal blocking: passes of up to tb_gens generations each; pass
+        // i (1-based) of n writes `out` when n - i is even, else the scratch
+        int rc = ensure_tb_plan(f);
+        if (rc) return rc;
+        const int64_t passes = (steps + f->tb_gens - 1) / f->tb_gens;
+        if (passes > 1) {
+            rc = ensure_buffer(&f->scratch, f->cells, "fractal_step: scratch allocation");
+            if (rc) return rc;
+        }
+        const uint8_t *src = in;
+        int64_t left = steps;
+        for (int64_t i = 1; i <= passes; ++i) {
+            uint8_t *dst = ((passes - i) % 2 == 0) ? out : f->scratch;
+            const int g = (int)std::min<int64_t>(left, f->tb_gens);
+            rc = launch_tb_once(f, src, dst, g, birth, survive, st);
+            if (rc) return rc;
+            left -= g;
+            src = dst;
+        }
+        return FR_OK;
+    }
     int rc = ensure_step_plan(f);
     if (rc) return rc;
     if (steps > 1) {
@@ -275,6 +299,32 @@ extern "C" int fractal_step(fractal_t *f, const uint8_t *in, uint8_t *out, int64
     return run_generations(in, out, f->scratch, steps, [&](const uint8_t *a, uint8_t *b) {
         return launch_step_once(f, a, b, birth, survive, st);
     });
+}
+
+extern "C" int fractal_set_temporal_blocking(fractal_t *f, int generations, int tile_levels)
+{
+    g_err.clear();
+    if (!f) return fail(FR_EINVAL, "fractal_set_temporal_blocking: handle is NULL");
+    if (generations < 0 || generations > kTbMaxGenerations)
+        return fail(FR_EINVAL, "fractal_set_temporal_blocking: generations must be in [0, 9]");
+    if (tile_levels != -1 && (tile_levels < 2 || tile_levels > f->r))
+        return fail(FR_EINVAL, "fractal_set_temporal_blocking: tile_levels must be -1 or in [2, r]");
+    const int old_g = f->tb_gens, old_l = f->tb_levels_user;
+    f->tb_gens = generations;
+    f->tb_levels_user = tile_levels;
+    if (generations > 0) {
+        if (tile_levels != old_l) {
+            cudaDeviceSynchronize();
+            free_tb_plan(f->tb);
+        }
+        const int rc = ensure_tb_plan(f);
+        if (rc) {
+            f->tb_gens = old_g;
+            f->tb_levels_user = old_l;
+            return rc;
+        }
+    }
+    return FR_OK;
 }
 
 extern "C" int fractal_bb_step(fractal_t *f, const uint8_t *in, uint8_t *out, int64_t steps,

@@ -66,6 +66,20 @@ struct BBPlan {
     int64_t local_words = 0, coarse_words = 0;
 };
 
+// Temporal blocking (temporal.cuh): tile depth, tables and launch shape of
+// the multi-generation pass for the carpet and the Vicsek fractal.
+struct TbPlan {
+    int L = -1;
+    int preset = -1;
+    int64_t KL = 0, NT = 0;
+    int nu = 0, nring = 0, W = 0, RS = 0, NWB = 0;
+    int off_halo = 0, off_pres = 0, off_box0 = 0, off_box1 = 0, off_mask = 0;
+    int smem = 0, block = 0, grid = 0, per_sm = 0;
+    uint16_t *upos = nullptr;
+    uint32_t *ring = nullptr;
+    int32_t *nbr = nullptr;
+};
+
 }  // namespace fr
 
 struct fractal {
@@ -86,6 +100,9 @@ struct fractal {
     uint8_t *host_io[2] = {nullptr, nullptr};  // device buffers of run_host
     int *status = nullptr;           // device word set by kernels whose bounded waits gave up
     std::atomic<int> server_refs{0}; // requests of a server not yet done (the plan must not change)
+    int tb_gens = 0;                 // temporal blocking: generations per pass (0 = off)
+    int tb_levels_user = -1;         // its tile depth (-1 = automatic)
+    fr::TbPlan tb;
     uint32_t test_extra_tx = 0;      // fractal_test_arm_timeout: next step launch's extra armed bytes
     uint32_t test_wait_limit = 0;    // ... and its wait limit (tries)
 };
@@ -93,6 +110,10 @@ struct fractal {
 namespace fr {
 
 int ensure_step_plan(fractal *f);
+int ensure_tb_plan(fractal *f);
+void free_tb_plan(TbPlan &p);
+int launch_tb_once(fractal *f, const uint8_t *in, uint8_t *out, int gens, uint32_t birth, uint32_t survive,
+                   cudaStream_t st);
 int ensure_bb_plan(fractal *f);
 void free_step_plan(StepPlan &p);
 void free_bb_plan(BBPlan &p);

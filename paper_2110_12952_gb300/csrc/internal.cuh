@@ -19,6 +19,7 @@ namespace fr {
 constexpr int kMaxSD = 256;     // max s^dim (digit tuples per level)
 constexpr int kMaxR = 62;       // max levels stored in tables
 constexpr int kMaxDirs = 27;    // 3^dim Moore offsets incl. the centre
+constexpr int kTbMaxGenerations = 9;   // temporal blocking: generations per pass (a 9-cell halo)
 
 // Unsigned division of x < 2^31 by a constant d >= 2 (Granlund & Montgomery,
 // "Division by invariant integers using multiplication", PLDI 1994, Thm 4.2

@@ -1589,6 +1589,7 @@ struct TapPolicy {
 #include "rows.cuh"
 #include "lid.cuh"
 #include "box3.cuh"
+#include "temporal.cuh"
 namespace fr {
 
 template <int DIM, int MODE>
@@ -2370,6 +2371,201 @@ int launch_step_multi(const fractal *cls, const InstDesc *descs, const int32_t *
     a.gen = gen;
     const int grid = (int)std::min<int64_t>((int64_t)cls->plan.per_sm * cls->num_sms, total);
     return dispatch<true>(cls, a, grid, nullptr, nullptr, st);
+}
+
+// ---------------------------------------------------------- temporal blocking
+
+void free_tb_plan(TbPlan &p)
+{
+    cudaFree(p.upos);
+    cudaFree(p.ring);
+    cudaFree(p.nbr);
+    p = TbPlan();
+}
+
+struct TbLayout {
+    int W = 0, NWB = 0, RS = 0, nring = 0;
+    int off_halo = 0, off_pres = 0, off_box0 = 0, off_box1 = 0, off_mask = 0, total = 0;
+};
+
+static TbLayout tb_layout(const fractal *f, int L)
+{
+    TbLayout y;
+    int nus = 1;
+    for (int i = 0; i < L - 2; ++i) nus *= 3;
+    const int64_t KL = ipow(f->k, L), NB = (int64_t)f->k * f->k;
+    y.W = 9 * nus + 18;
+    y.NWB = (y.W + 31) / 32;
+    y.RS = y.NWB + 2;
+    y.nring = 4 * nus + 4;   // at most: the unit ring around the tile's unit grid
+    const int64_t boxb = round16(4 * (int64_t)y.W * y.RS);
+    int64_t off = round16(KL);
+    y.off_halo = (int)off;
+    off = round16(off + NB * y.nring + 4);
+    y.off_pres = (int)off;
+    off = round16(off + y.nring + 4);
+    y.off_box0 = (int)off;
+    y.off_box1 = (int)(off + boxb);
+    y.off_mask = (int)(off + 2 * boxb);
+    const int64_t total = off + 3 * boxb;
+    y.total = total > (1 << 30) ? (1 << 30) : (int)total;
+    return y;
+}
+
+int ensure_tb_plan(fractal *f)
+{
+    const int P = rows_preset_of(f);
+    if (P < 0) {
+        set_error(FR_EINVAL, "temporal blocking: only the carpet and the Vicsek fractal (preset offsets)");
+        return FR_EINVAL;
+    }
+    int L = f->tb_levels_user;
+    if (L < 0) {
+        // the deepest tile whose shared memory stays within 100 KB
+        L = -1;
+        for (int l = 2; l <= std::min(f->r, 6); ++l)
+            if (tb_layout(f, l).total <= 100 * 1024 && ipow(f->k, f->r - l) < ((int64_t)1 << 31)) L = l;
+    }
+    if (L < 2 || L > f->r) {
+        set_error(FR_EINVAL, "temporal blocking: needs a tile depth of at least 2 levels");
+        return FR_EINVAL;
+    }
+    if (f->tb.L == L && f->tb.upos) return FR_OK;
+    free_tb_plan(f->tb);
+    int rc = ensure_status(f);
+    if (rc) return rc;
+    const TbLayout y = tb_layout(f, L);
+    int optin = 0, dev = 0;
+    FR_CUDA(cudaGetDevice(&dev));
+    FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (y.total > optin) {
+        set_error(FR_EINVAL, "temporal blocking: tile does not fit in shared memory");
+        return FR_EINVAL;
+    }
+    TbPlan p;
+    p.L = L;
+    p.preset = P;
+    p.KL = ipow(f->k, L);
+    p.NT = ipow(f->k, f->r - L);
+    if (p.NT >= ((int64_t)1 << 31)) {
+        set_error(FR_EOVERFLOW, "temporal blocking: more than 2^31 tiles at this tile depth");
+        return FR_EOVERFLOW;
+    }
+    int nus = 1, nu = 1;
+    for (int i = 0; i < L - 2; ++i) {
+        nus *= 3;
+        nu *= f->k;
+    }
+    p.nu = nu;
+    // unit grid of a tile (the unit layout of rows_layout.h against the fractal's own lambda)
+    std::vector<int> M((size_t)nus * nus, -1);
+    std::vector<uint16_t> upos(nu);
+    const int NB = f->k * f->k;
+    for (int q = 0; q < nu; ++q) {
+        int c[3];
+        host_lambda(f, q, L - 2, c);
+        M[(size_t)c[1] * nus + c[0]] = q;
+        upos[q] = (uint16_t)((c[0] + 1) | ((c[1] + 1) << 8));
+        for (int u = 0; u < NB; ++u) {
+            int d[3];
+            host_lambda(f, (int64_t)NB * q + u, L, d);
+            const int ex = 9 * c[0] + (P == 0 ? rp_x<0>(u) : rp_x<1>(u));
+            const int ey = 9 * c[1] + (P == 0 ? rp_y<0>(u) : rp_y<1>(u));
+            if (d[0] != ex || d[1] != ey) {
+                set_error(FR_EINVAL, "temporal blocking: unit layout does not match the fractal");
+                return FR_EINVAL;
+            }
+        }
+    }
+    // the ring of units of the neighbouring tiles around the tile's unit grid
+    std::vector<uint32_t> ring;
+    for (int by = 0; by < nus + 2; ++by)
+        for (int bx = 0; bx < nus + 2; ++bx) {
+            if (bx > 0 && bx < nus + 1 && by > 0 && by < nus + 1) continue;
+            const int gx = bx - 1, gy = by - 1;
+            const int tdx = gx < 0 ? -1 : (gx >= nus ? 1 : 0), tdy = gy < 0 ? -1 : (gy >= nus ? 1 : 0);
+            const int lu = M[(size_t)((gy + nus) % nus) * nus + (gx + nus) % nus];
+            if (lu < 0) continue;
+            const int d9 = (tdx + 1) + 3 * (tdy + 1);
+            const int slot = d9 < 4 ? d9 : d9 - 1;
+            ring.push_back((uint32_t)lu | ((uint32_t)slot << 24));
+            ring.push_back((uint32_t)bx | ((uint32_t)by << 8));
+        }
+    p.nring = (int)ring.size() / 2;
+    if (p.nring > y.nring) {
+        set_error(FR_EINVAL, "temporal blocking: halo ring larger than planned");
+        return FR_EINVAL;
+    }
+    p.W = y.W;
+    p.RS = y.RS;
+    p.NWB = y.NWB;
+    p.off_halo = y.off_halo;
+    p.off_pres = y.off_pres;
+    p.off_box0 = y.off_box0;
+    p.off_box1 = y.off_box1;
+    p.off_mask = y.off_mask;
+    p.smem = y.total;
+    p.block = (p.W * p.NWB >= 1024 || nu >= 256) ? 256 : 128;
+    FR_CUDA(cudaMalloc(&p.upos, upos.size() * sizeof(uint16_t)));
+    FR_CUDA(cudaMemcpy(p.upos, upos.data(), upos.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    FR_CUDA(cudaMalloc(&p.ring, std::max<size_t>(ring.size(), 2) * sizeof(uint32_t)));
+    if (!ring.empty())
+        FR_CUDA(cudaMemcpy(p.ring, ring.data(), ring.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    cudaError_t e = cudaMalloc(&p.nbr, (size_t)p.NT * 8 * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        free_tb_plan(p);
+        return cuda_fail(e, "temporal blocking: neighbour table allocation");
+    }
+    {
+        const int64_t g = std::min<int64_t>((p.NT + 255) / 256, (int64_t)f->num_sms * 16);
+        nbr_table_kernel<<<(int)std::max<int64_t>(g, 1), 256>>>(f->dev, p.NT, f->r - L,
+                                                                (int32_t)ipow(f->s, f->r - L), 8, p.nbr);
+        FR_CUDA(cudaGetLastError());
+        FR_CUDA(cudaDeviceSynchronize());
+    }
+    auto kfn = P == 0 ? step_tb_kernel<0> : step_tb_kernel<1>;
+    FR_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p.per_sm, kfn, p.block, p.smem));
+    if (p.per_sm < 1) {
+        free_tb_plan(p);
+        set_error(FR_EINVAL, "temporal blocking: tile does not fit in shared memory");
+        return FR_EINVAL;
+    }
+    p.grid = (int)std::min<int64_t>((int64_t)p.per_sm * f->num_sms, p.NT);
+    f->tb = p;
+    return FR_OK;
+}
+
+int launch_tb_once(fractal *f, const uint8_t *in, uint8_t *out, int gens, uint32_t birth, uint32_t survive,
+                   cudaStream_t st)
+{
+    const TbPlan &p = f->tb;
+    TbArgs a;
+    a.KL = p.KL;
+    a.NT = p.NT;
+    a.nu = p.nu;
+    a.nring = p.nring;
+    a.W = p.W;
+    a.RS = p.RS;
+    a.NWB = p.NWB;
+    a.gens = gens;
+    a.birth = birth;
+    a.survive = survive;
+    a.upos = p.upos;
+    a.ring = p.ring;
+    a.nbr = p.nbr;
+    a.off_halo = p.off_halo;
+    a.off_pres = p.off_pres;
+    a.off_box0 = p.off_box0;
+    a.off_box1 = p.off_box1;
+    a.off_mask = p.off_mask;
+    a.status = f->status;
+    if (p.preset == 0)
+        step_tb_kernel<0><<<p.grid, p.block, p.smem, st>>>(a, in, out);
+    else
+        step_tb_kernel<1><<<p.grid, p.block, p.smem, st>>>(a, in, out);
+    FR_CUDA(cudaGetLastError());
+    return FR_OK;
 }
 
 // ---------------------------------------------------------------- autotune

@@ -175,6 +175,11 @@ class Fractal:
     def tile_levels(self, levels: int):
         self._check(self._lib.fractal_set_tile_levels(self._h, int(levels)))
 
+    def set_temporal_blocking(self, generations: int, tile_levels: int = -1):
+        """``fractal_set_temporal_blocking``: up to ``generations`` (1..9)
+        generations per pass of ``step``; 0 turns it off."""
+        self._check(self._lib.fractal_set_temporal_blocking(self._h, int(generations), int(tile_levels)))
+
     @property
     def pipeline_stages(self) -> int:
         """Input pipeline stages of the step's plan (``fractal_plan_info``)."""
