@@ -643,6 +643,43 @@ def batched_compare(args, W):
     return res
 
 
+def temporal_compare(g, x, y, single_ms, peak):
+    """Temporal blocking on the carpet: one pass = 9 generations
+    (fractal_set_temporal_blocking(9), automatic tile depth).  Bytes per
+    update are reported next to the 2-byte single-generation figure: per
+    tile of k^L cells a pass reads the tile and the level-2 units of the
+    neighbouring tiles that touch it, and writes the tile."""
+    gens = 9
+    g.set_temporal_blocking(gens)
+    times = time_steps(lambda: g.step(x, out=y, steps=gens), 10, 3)
+    g.set_temporal_blocking(0)
+    ms = statistics.median(times)
+    L = next(l for l in range(5, 1, -1) if l <= g.r and _tb_smem(l) <= 100 * 1024)
+    tile = 8 ** L
+    halo_units = 4 * 3 ** (L - 2) + 4
+    bytes_per_pass = g.cells // tile * (2 * tile + 64 * halo_units)
+    return {"generations_per_pass": gens, "tile_levels": L, "ms_per_pass": ms,
+            "updates_per_s": g.cells * gens / (ms / 1e3),
+            "speedup_vs_single_generation": single_ms * gens / ms,
+            "hbm_bytes_per_update": bytes_per_pass / (g.cells * gens),
+            "achieved_gbs": bytes_per_pass / (ms / 1e3) / 1e9, "peak_gbs": peak,
+            "note": "bytes per update are (tile + halo units + tile) / (cells x generations); "
+                    "the roofline of single generations is 2 B per update"}
+
+
+def _tb_smem(L):
+    # shared memory of the temporal-blocking plan at tile depth L (carpet)
+    r16 = lambda v: (v + 15) // 16 * 16
+    nus = 3 ** (L - 2)
+    W_ = 9 * nus + 18
+    RS = (W_ + 31) // 32 + 2
+    nring = 4 * nus + 4
+    off = r16(8 ** L)
+    off = r16(off + 64 * nring + 4)
+    off = r16(off + nring + 4)
+    return off + 3 * r16(4 * W_ * RS)
+
+
 def others_compare(args, W):
     """Carpet r=10, Vicsek r=12, Menger r=6 (p 0.5, seeds 4-6; Menger B5/S45):
     one generation per timed step after autotuning the tile depth; states
@@ -676,6 +713,8 @@ def others_compare(args, W):
                         "bb_hbm_frac": 2.0 * g.box_cells / (bms / 1e3) / 1e9 / peak,
                         "speedup_compact_vs_bb": bms / ms})
             del box, bo
+        if inst.family.name == "carpet":
+            res["temporal_blocking"] = temporal_compare(g, x, y, ms, peak)
         out[f"{inst.family.name}_r{inst.r}"] = res
         g.close()
         torch.cuda.empty_cache()

@@ -2523,9 +2523,14 @@ int ensure_tb_plan(fractal *f)
         FR_CUDA(cudaGetLastError());
         FR_CUDA(cudaDeviceSynchronize());
     }
-    auto kfn = P == 0 ? step_tb_kernel<0> : step_tb_kernel<1>;
+    auto kfn = P == 0 ? step_tb_kernel<0, false> : step_tb_kernel<1, false>;
+    auto kfl = P == 0 ? step_tb_kernel<0, true> : step_tb_kernel<1, true>;
     FR_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(kfl, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    int per_sm_life = 0;
     FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p.per_sm, kfn, p.block, p.smem));
+    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_life, kfl, p.block, p.smem));
+    p.per_sm = std::min(p.per_sm, per_sm_life);
     if (p.per_sm < 1) {
         free_tb_plan(p);
         set_error(FR_EINVAL, "temporal blocking: tile does not fit in shared memory");
@@ -2560,10 +2565,15 @@ int launch_tb_once(fractal *f, const uint8_t *in, uint8_t *out, int gens, uint32
     a.off_box1 = p.off_box1;
     a.off_mask = p.off_mask;
     a.status = f->status;
-    if (p.preset == 0)
-        step_tb_kernel<0><<<p.grid, p.block, p.smem, st>>>(a, in, out);
+    const bool life = birth == 0x8u && survive == 0xCu;   // B3/S23
+    if (p.preset == 0 && life)
+        step_tb_kernel<0, true><<<p.grid, p.block, p.smem, st>>>(a, in, out);
+    else if (p.preset == 0)
+        step_tb_kernel<0, false><<<p.grid, p.block, p.smem, st>>>(a, in, out);
+    else if (life)
+        step_tb_kernel<1, true><<<p.grid, p.block, p.smem, st>>>(a, in, out);
     else
-        step_tb_kernel<1><<<p.grid, p.block, p.smem, st>>>(a, in, out);
+        step_tb_kernel<1, false><<<p.grid, p.block, p.smem, st>>>(a, in, out);
     FR_CUDA(cudaGetLastError());
     return FR_OK;
 }

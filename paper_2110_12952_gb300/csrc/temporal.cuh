@@ -15,11 +15,12 @@
 // every present unit; nothing for holes and for absent neighbouring tiles),
 // and every generation's result is masked with it, so non-members stay dead.
 //
-// Per generation and 32 box cells: 9 word loads, 6 funnel shifts for the
-// west/east neighbours of three rows, 14 logic operations for the 8-input
-// bit-sliced adder (count bits b3..b0), 17 for the rule (a multiplexer tree
-// over the count bits with the birth/survival tables as all-ones or all-zero
-// words), the mask and a store.  HBM bytes per cell-update: (tile + halo
+// Per generation and 32 box cells: 3 word loads (a thread walks down a word
+// column keeping three rows in registers), 6 funnel shifts for the west/east
+// neighbours, 14 logic operations for the 8-input bit-sliced adder (count
+// bits b3..b0), the rule (3 for B3/S23, else 17: a multiplexer tree over the
+// count bits with the birth/survival tables as all-ones or all-zero words),
+// the mask and a store.  HBM bytes per cell-update: (tile + halo
 // units + tile) / (tile cells x generations) instead of 2.
 #pragma once
 
@@ -110,14 +111,17 @@ __device__ __forceinline__ void tb_gather_words(const uint32_t *t, uint32_t *o, 
     ((o[I] = assemble<TotalWord<P, I>>(nullptr, nullptr, t)), ...);
 }
 
-// One generation of box word (y, w) (w = 1..NWB): Life-like rule over the 8
-// Moore neighbours, bit-sliced, masked.
-__device__ __forceinline__ uint32_t tb_cell_word(const uint32_t *s, int RS, uint32_t m, const uint32_t *tb,
-                                                 const uint32_t *ts)
+// One generation of a box word from the words of its row and the rows
+// above (a) and below (e), each with its west (_m) and east (_p) neighbour
+// words: Life-like rule over the 8 Moore neighbours, bit-sliced, masked.
+// LIFE: the rule is B3/S23 (new = count is 3, or 2 and alive); otherwise
+// tb / ts hold the birth / survival tables for counts 0..8 as all-ones or
+// zero words.
+template <bool LIFE>
+__device__ __forceinline__ uint32_t tb_cell_word(uint32_t a_m, uint32_t a, uint32_t a_p, uint32_t c_m, uint32_t c,
+                                                 uint32_t c_p, uint32_t e_m, uint32_t e, uint32_t e_p, uint32_t m,
+                                                 const uint32_t *tb, const uint32_t *ts)
 {
-    const uint32_t a_m = s[-RS - 1], a = s[-RS], a_p = s[-RS + 1];
-    const uint32_t c_m = s[-1], c = s[0], c_p = s[1];
-    const uint32_t e_m = s[RS - 1], e = s[RS], e_p = s[RS + 1];
     const uint32_t aW = __funnelshift_l(a_m, a, 1), aE = __funnelshift_r(a, a_p, 1);
     const uint32_t cW = __funnelshift_l(c_m, c, 1), cE = __funnelshift_r(c, c_p, 1);
     const uint32_t eW = __funnelshift_l(e_m, e, 1), eE = __funnelshift_r(e, e_p, 1);
@@ -128,19 +132,22 @@ __device__ __forceinline__ uint32_t tb_cell_word(const uint32_t *s, int RS, uint
     const uint32_t b0 = s0 ^ s1 ^ s2, k3 = (s0 & s1) | (s2 & (s0 ^ s1));
     const uint32_t t0 = k0 ^ k1 ^ k2, d0 = (k0 & k1) | (k2 & (k0 ^ k1));
     const uint32_t b1 = t0 ^ k3, d1 = t0 & k3;
-    const uint32_t b2 = d0 ^ d1, b3 = d0 & d1;
-    // rule: multiplexer over the count bits; tb / ts: birth / survival table
-    // entries for counts 0..8 as all-ones or zero words
-    const uint32_t nb = tb_sel(b3, tb[8],
-                               tb_sel(b2, tb_sel(b1, tb_sel(b0, tb[7], tb[6]), tb_sel(b0, tb[5], tb[4])),
-                                      tb_sel(b1, tb_sel(b0, tb[3], tb[2]), tb_sel(b0, tb[1], tb[0]))));
-    const uint32_t ns = tb_sel(b3, ts[8],
-                               tb_sel(b2, tb_sel(b1, tb_sel(b0, ts[7], ts[6]), tb_sel(b0, ts[5], ts[4])),
-                                      tb_sel(b1, tb_sel(b0, ts[3], ts[2]), tb_sel(b0, ts[1], ts[0]))));
-    return tb_sel(c, ns, nb) & m;
+    if constexpr (LIFE) {
+        // count 2 or 3 (b1 set, no 4 or 8), and b0 or alive: d0 | d1 is 4 or 8
+        return b1 & ~(d0 | d1) & (b0 | c) & m;
+    } else {
+        const uint32_t b2 = d0 ^ d1, b3 = d0 & d1;
+        const uint32_t nb = tb_sel(b3, tb[8],
+                                   tb_sel(b2, tb_sel(b1, tb_sel(b0, tb[7], tb[6]), tb_sel(b0, tb[5], tb[4])),
+                                          tb_sel(b1, tb_sel(b0, tb[3], tb[2]), tb_sel(b0, tb[1], tb[0]))));
+        const uint32_t ns = tb_sel(b3, ts[8],
+                                   tb_sel(b2, tb_sel(b1, tb_sel(b0, ts[7], ts[6]), tb_sel(b0, ts[5], ts[4])),
+                                          tb_sel(b1, tb_sel(b0, ts[3], ts[2]), tb_sel(b0, ts[1], ts[0]))));
+        return tb_sel(c, ns, nb) & m;
+    }
 }
 
-template <int P>
+template <int P, bool LIFE>
 __global__ void __launch_bounds__(256) step_tb_kernel(TbArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     constexpr int NB = RowsPreset<P>::k * RowsPreset<P>::k, NW = (NB + 3) / 4;
@@ -160,6 +167,8 @@ __global__ void __launch_bounds__(256) step_tb_kernel(TbArgs a, const uint8_t *_
         tsl[j] = ((a.survive >> j) & 1u) ? 0xffffffffu : 0u;
     }
     for (int i = tid; i < boxw; i += nth) box1[i] = 0;   // its guard words stay 0
+    const int nstrip = nth / a.NWB;                     // strips of rows per word column
+    const int my_strip = tid / a.NWB, my_w = 1 + tid % a.NWB;
     for (int64_t T = blockIdx.x; T < a.NT; T += gridDim.x) {
         // 1. the tile's bytes and the present halo units, into shared memory;
         // the state and mask boxes cleared
@@ -211,14 +220,27 @@ __global__ void __launch_bounds__(256) step_tb_kernel(TbArgs a, const uint8_t *_
             tb_scatter_unit<P>(u, box0, mask, a.RS, bx, by, std::make_integer_sequence<int, 9>());
         }
         __syncthreads();
-        // 3. the generations, each over the rows it can still compute exactly
+        // 3. the generations, each over the rows it can still compute
+        // exactly: thread (strip, w) walks down word column w of its strip of
+        // rows, keeping three rows of three words in registers
         uint32_t *cur = box0, *nxt = box1;
         for (int j = 1; j <= a.gens; ++j) {
             const int rows = a.W - 2 * j;
-            for (int i = tid; i < rows * a.NWB; i += nth) {
-                const int y = j + i / a.NWB, w = 1 + i % a.NWB;
-                const int at = y * a.RS + w;
-                nxt[at] = tb_cell_word(cur + at, a.RS, mask[at], tbl, tsl);
+            const int len = (rows + nstrip - 1) / nstrip;
+            const int y0 = j + my_strip * len, y1 = min(y0 + len, a.W - j);
+            if (my_strip < nstrip && y0 < y1) {
+                const uint32_t *sp = cur + (y0 - 1) * a.RS + my_w;
+                uint32_t a_m = sp[-1], a0 = sp[0], a_p = sp[1];
+                sp += a.RS;
+                uint32_t c_m = sp[-1], c0 = sp[0], c_p = sp[1];
+                for (int y = y0; y < y1; ++y) {
+                    sp += a.RS;
+                    const uint32_t e_m = sp[-1], e0 = sp[0], e_p = sp[1];
+                    const int at = y * a.RS + my_w;
+                    nxt[at] = tb_cell_word<LIFE>(a_m, a0, a_p, c_m, c0, c_p, e_m, e0, e_p, mask[at], tbl, tsl);
+                    a_m = c_m; a0 = c0; a_p = c_p;
+                    c_m = e_m; c0 = e0; c_p = e_p;
+                }
             }
             __syncthreads();
             uint32_t *t = cur;
