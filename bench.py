@@ -703,6 +703,8 @@ def others_compare(args, W):
         res = {"cells": g.cells, "tile_levels": L, "ms_per_generation": ms,
                "updates_per_s": g.cells / (ms / 1e3), "hbm_frac": 2.0 * g.cells / (ms / 1e3) / 1e9 / peak,
                "l2_flush": small}
+        if inst.family.name == "carpet":
+            res["temporal_blocking"] = temporal_compare(g, x, y, ms, peak)
         if g.box_cells <= 4 * 2**30:
             box = g.scatter(x)
             del x, y
@@ -713,8 +715,6 @@ def others_compare(args, W):
                         "bb_hbm_frac": 2.0 * g.box_cells / (bms / 1e3) / 1e9 / peak,
                         "speedup_compact_vs_bb": bms / ms})
             del box, bo
-        if inst.family.name == "carpet":
-            res["temporal_blocking"] = temporal_compare(g, x, y, ms, peak)
         out[f"{inst.family.name}_r{inst.r}"] = res
         g.close()
         torch.cuda.empty_cache()

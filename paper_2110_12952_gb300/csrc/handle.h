@@ -18,6 +18,8 @@ namespace fr {
 // embedding.  The local lambda table `pos` (identical for every tile) gives
 // each cell's offset in a shared-memory box padded by one halo cell per side.
 struct StepPlan {
+    int built_levels = -2; // the handle's tile-depth and stage settings the plan was built for
+    int built_stages = -2;
     int L = -1;            // tile levels
     int64_t KL = 0;        // k^L cells per tile
     int64_t NT = 0;        // k^(r-L) tiles

@@ -846,8 +846,11 @@ static constexpr uint32_t kZeroSel = 0x8;
 
 int ensure_step_plan(fractal *f)
 {
+    // the plan depends only on the fractal and on these two settings (the
+    // tables behind the automatic choice are too costly to rebuild per call)
+    if (f->plan.pos && f->plan.built_levels == f->tile_levels_user && f->plan.built_stages == f->stages_user)
+        return FR_OK;
     int L = choose_levels(f);
-    if (f->plan.L == L && f->plan.pos && f->plan.nstage == (int)plan_layout(f, L).nstage) return FR_OK;
     free_step_plan(f->plan);
     int rc = ensure_status(f);
     if (rc) return rc;
@@ -1060,6 +1063,8 @@ int ensure_step_plan(fractal *f)
         free_step_plan(p);
         return rc;
     }
+    p.built_levels = f->tile_levels_user;
+    p.built_stages = f->stages_user;
     f->plan = p;
     return FR_OK;
 }
