@@ -555,6 +555,20 @@ def bb_compare(args, W):
     box_out = torch.empty_like(box)
     bt = time_steps(lambda: g.bb_step(box, out=box_out, steps=1), n, 3)
     c_ms, b_ms = statistics.median(ct), statistics.median(bt)
+    # the paper's own approaches at the same level (Sec. 4): lambda(omega) on
+    # the box and nu(omega) on blocked rho x rho storage, rho = 2 .. 32
+    paper = {}
+    for l in range(1, 6):
+        rho = 2 ** l
+        lt = time_steps(lambda: g.lambda_box_step(box, l, out=box_out, steps=1), max(3, n // 2), 2)
+        blk = g.blocked_pack(st, l)
+        blk_out = torch.empty_like(blk)
+        kt = time_steps(lambda: g.blocked_step(blk, l, out=blk_out, steps=1), max(3, n // 2), 2,
+                        flush=flush if 2 * blk.numel() < 4 * 129 * 2**20 else None)
+        lm, km = statistics.median(lt), statistics.median(kt)
+        paper[f"rho{rho}"] = {"lambda_box_ms": lm, "blocked_nu_ms": km, "blocked_bytes": blk.numel(),
+                              "speedup_vs_bb_lambda": b_ms / lm, "speedup_vs_bb_blocked_nu": b_ms / km}
+        del blk, blk_out
     res = {"workload": f"sierpinski_triangle_F32_r{r}", "cells": g.cells, "box_cells": g.box_cells,
            "compact_updates_per_s": g.cells / (c_ms / 1e3),
            "compact_ms_per_generation": c_ms,
@@ -566,7 +580,11 @@ def bb_compare(args, W):
            "bb_hbm_frac": 2.0 * g.box_cells / (b_ms / 1e3) / 1e9 / peak,
            "speedup_compact_vs_bb": b_ms / c_ms,
            "memory_ratio_bb_vs_compact": g.box_cells / g.cells,
-           "generations_timed": n}
+           "generations_timed": n,
+           "paper_approaches": paper,
+           "paper_approaches_note": "lambda_box: the paper's lambda(omega) (box storage, compact grid of "
+                                    "rho x rho blocks); blocked_nu: its nu(omega) on blocked rho x rho storage "
+                                    "(mini box staged in shared memory, maps per block); speedups vs this BB kernel"}
     del st, out, box, box_out, flush_buf
     g.close()
     torch.cuda.empty_cache()

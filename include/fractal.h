@@ -171,6 +171,38 @@ int fractal_bb_step(fractal_t *f, const uint8_t *box_in_dev, uint8_t *box_out_de
                     int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
                     void *stream);
 
+/* ---- The paper's own two approaches, as baselines (Sec. 4) -------------
+ * rho_levels = l in [1, r] with rho = s^l and rho^dim <= 1024.
+ *
+ * "lambda(omega)": the state stays in the n^dim box (as for fractal_bb_step),
+ * but only the blocks of threads the fractal needs run: block b covers the
+ * rho^dim box cells of coarse cell lambda(b) of the level r - l fractal, and
+ * threads on members read their neighbours straight from the box.  box_in_dev
+ * must hold 0 on every cell off the fractal (as fractal_scatter_to_box
+ * writes); box_out_dev's cells off the fractal are not written (keep them 0).
+ * steps >= 1; for steps > 1 the library ping-pongs through a zeroed box. */
+int fractal_lambda_box_step(fractal_t *f, int rho_levels, const uint8_t *box_in_dev,
+                            uint8_t *box_out_dev, int64_t steps, uint32_t birth_mask,
+                            uint32_t survive_mask, void *stream);
+/* Blocked storage (Sec. 3, the blocked approach): k^(r-l) mini boxes of
+ * rho^dim bytes, mini box b (coarse cell b in compact order) holding the
+ * cells of the level-l sub-fractal b at their positions in its rho^dim box
+ * (x fastest), 0 elsewhere.  fractal_blocked_info gives the layout's bytes;
+ * pack / unpack convert from / to compact order (pack writes every byte). */
+int fractal_blocked_info(fractal_t *f, int rho_levels, int64_t *bytes);
+int fractal_blocked_pack(fractal_t *f, int rho_levels, const uint8_t *compact_dev,
+                         uint8_t *blocked_dev, void *stream);
+int fractal_blocked_unpack(fractal_t *f, int rho_levels, const uint8_t *blocked_dev,
+                           uint8_t *compact_dev, void *stream);
+/* "nu(omega)" on blocked storage: one block per mini box stages it in shared
+ * memory and maps its 3^dim - 1 neighbouring coarse cells once (coarse lambda,
+ * a Moore move, coarse nu); members read neighbours inside the block from
+ * shared memory and across its edge from the neighbouring mini boxes.  in /
+ * out: blocked layouts of the same rho, not overlapping. */
+int fractal_blocked_step(fractal_t *f, int rho_levels, const uint8_t *in_dev, uint8_t *out_dev,
+                         int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
+                         void *stream);
+
 /* Compact <-> box views (through lambda).  scatter writes every box byte:
  * box_dev[lambda(omega)] = compact_dev[omega] != 0, and 0 off the fractal.
  * gather: compact_dev[omega] = box_dev[lambda(omega)] != 0. */

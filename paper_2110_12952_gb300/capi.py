@@ -69,6 +69,11 @@ SIGNATURES = {
     "fractal_set_pipeline_stages": (c_int, [c_fp, c_int]),
     "fractal_nu_tc": (c_int, [c_fp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "fractal_set_temporal_blocking": (c_int, [c_fp, c_int, c_int]),
+    "fractal_lambda_box_step": (c_int, [c_fp, c_int, c_vp, c_vp, c_i64, c_u32, c_u32, c_vp]),
+    "fractal_blocked_info": (c_int, [c_fp, c_int, c_i64p]),
+    "fractal_blocked_pack": (c_int, [c_fp, c_int, c_vp, c_vp, c_vp]),
+    "fractal_blocked_unpack": (c_int, [c_fp, c_int, c_vp, c_vp, c_vp]),
+    "fractal_blocked_step": (c_int, [c_fp, c_int, c_vp, c_vp, c_i64, c_u32, c_u32, c_vp]),
     "fractal_lambda_tc": (c_int, [c_fp, c_vp, c_i64, c_vp, c_vp]),
     "fractal_shard_plan": (c_int, [c_int, c_int, c_int, c_int, c_i32p, c_int, c_int, c_int, ctypes.POINTER(c_vp)]),
     "fractal_shard_destroy": (c_int, [c_vp]),

@@ -152,6 +152,7 @@ extern "C" int fractal_destroy(fractal_t *f)
     cudaDeviceSynchronize();
     free_step_plan(f->plan);
     free_tb_plan(f->tb);
+    fr_paper_aux_free(f);
     free_bb_plan(f->bb);
     cudaFree(f->scratch);
     cudaFree(f->bb_scratch);

@@ -105,6 +105,7 @@ struct fractal {
     int tb_gens = 0;                 // temporal blocking: generations per pass (0 = off)
     int tb_levels_user = -1;         // its tile depth (-1 = automatic)
     fr::TbPlan tb;
+    void *paper_aux = nullptr;       // the paper's approaches (paper_kernels.cu): geometry and scratch
     uint32_t test_extra_tx = 0;      // fractal_test_arm_timeout: next step launch's extra armed bytes
     uint32_t test_wait_limit = 0;    // ... and its wait limit (tries)
 };
@@ -113,6 +114,7 @@ namespace fr {
 
 int ensure_step_plan(fractal *f);
 int ensure_tb_plan(fractal *f);
+void fr_paper_aux_free(fractal *f);
 void free_tb_plan(TbPlan &p);
 int launch_tb_once(fractal *f, const uint8_t *in, uint8_t *out, int gens, uint32_t birth, uint32_t survive,
                    cudaStream_t st);

@@ -175,6 +175,45 @@ class Fractal:
     def tile_levels(self, levels: int):
         self._check(self._lib.fractal_set_tile_levels(self._h, int(levels)))
 
+    # ------------------------------------------- the paper's approaches
+    def lambda_box_step(self, box: torch.Tensor, rho_levels: int, out: torch.Tensor | None = None,
+                        steps: int = 1, rule=None, stream=None) -> torch.Tensor:
+        """``fractal_lambda_box_step``: the paper's lambda(omega) approach on a
+        box whose cells off the fractal are 0."""
+        rule = rule or self.default_rule()
+        out = out if out is not None else torch.zeros_like(box)
+        self._check(self._lib.fractal_lambda_box_step(self._h, int(rho_levels), _dev_ptr(box, torch.uint8, "box"),
+                                                      _dev_ptr(out, torch.uint8, "out"), steps, rule[0], rule[1],
+                                                      _stream(stream)))
+        return out
+
+    def blocked_bytes(self, rho_levels: int) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.fractal_blocked_info(self._h, int(rho_levels), ctypes.byref(v)))
+        return v.value
+
+    def blocked_pack(self, compact: torch.Tensor, rho_levels: int, stream=None) -> torch.Tensor:
+        out = torch.empty(self.blocked_bytes(rho_levels), dtype=torch.uint8, device=compact.device)
+        self._check(self._lib.fractal_blocked_pack(self._h, int(rho_levels), _dev_ptr(compact, torch.uint8, "compact"),
+                                                   out.data_ptr(), _stream(stream)))
+        return out
+
+    def blocked_unpack(self, blocked: torch.Tensor, rho_levels: int, stream=None) -> torch.Tensor:
+        out = torch.empty(self.cells, dtype=torch.uint8, device=blocked.device)
+        self._check(self._lib.fractal_blocked_unpack(self._h, int(rho_levels), _dev_ptr(blocked, torch.uint8, "blocked"),
+                                                     out.data_ptr(), _stream(stream)))
+        return out
+
+    def blocked_step(self, blocked: torch.Tensor, rho_levels: int, out: torch.Tensor | None = None, steps: int = 1,
+                     rule=None, stream=None) -> torch.Tensor:
+        """``fractal_blocked_step``: the paper's nu(omega) approach on blocked storage."""
+        rule = rule or self.default_rule()
+        out = out if out is not None else torch.empty_like(blocked)
+        self._check(self._lib.fractal_blocked_step(self._h, int(rho_levels), _dev_ptr(blocked, torch.uint8, "blocked"),
+                                                   _dev_ptr(out, torch.uint8, "out"), steps, rule[0], rule[1],
+                                                   _stream(stream)))
+        return out
+
     def set_temporal_blocking(self, generations: int, tile_levels: int = -1):
         """``fractal_set_temporal_blocking``: up to ``generations`` (1..9)
         generations per pass of ``step``; 0 turns it off."""
