@@ -161,7 +161,7 @@ __global__ void blocked_step_kernel(int dim, int rho, int vol, int64_t coarse, c
     for (int64_t b = blockIdx.x; b < coarse; b += gridDim.x) {
         __syncthreads();
         mini[t] = in[b * vol + t];
-        if (t < nd) nbs[t] = nbt[b * 26 + t];
+        for (int q = t; q < nd; q += blockDim.x) nbs[q] = nbt[b * 26 + q];   // blocks of 4 or 8 threads too
         __syncthreads();
         if (!member) {
             out[b * vol + t] = 0;
