@@ -182,7 +182,7 @@ __global__ void blocked_step_kernel(int dim, int rho, int vol, int64_t coarse, c
                     if (!ox && !oy && !oz) {
                         count += mini[o] != 0;
                     } else {
-                        const int q = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+                        const int q = (ox + 1) + 3 * (oy + 1) + (dim == 3 ? 9 * (oz + 1) : 0);
                         const int centre = dim == 3 ? 13 : 4;
                         const int32_t nbk = nbs[q < centre ? q : q - 1];
                         if (nbk >= 0) count += in[(int64_t)nbk * vol + o] != 0;
