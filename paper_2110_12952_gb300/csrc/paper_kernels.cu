@@ -34,7 +34,7 @@ static int pk_fail(const std::string &msg)
 // The local geometry of a blocked layout: rho = s^l, the local membership
 // bitmap (rho^dim bits, x fastest) and its local omega -> mini-box offset.
 struct PkLocal {
-    int l = 0, rho = 0, vol = 0;        // rho^dim
+    int l = -1, rho = 0, vol = 0;       // rho^dim
     int64_t kl = 0;                     // k^l members per mini box
     int64_t coarse = 0;                 // k^(r-l) mini boxes
     uint32_t *bits = nullptr;           // device, (vol + 31) / 32 words
@@ -258,6 +258,7 @@ void fr::fr_paper_aux_free(fractal *f)
 
 static int pk_prepare(fractal *f, int l, bool need_nb, PkLocal **out)
 {
+    if (l < 1 || l > f->r) return pk_fail("rho_levels must be in [1, r]");
     PkCache *c = pk_cache(f);
     if (c->loc.l != l) {
         pk_free(c->loc);
