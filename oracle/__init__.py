@@ -78,6 +78,18 @@ def _declare(lib):
         "oracle_bernoulli_threshold": (U64, [D]),
         "oracle_init_bernoulli": (None, [U64, D, _u8p, L, L]),
     }
+    mx = [I, I, I, _i32p, _i32p]   # s, r, dim, ks, offs
+    sig.update({
+        "oracle_mix_cells": (L, [I, _i32p]),
+        "oracle_mix_lambda_batch": (None, mx + [_i64p, L, _i64p]),
+        "oracle_mix_nu_batch": (None, mx + [_i64p, L, _i64p]),
+        "oracle_mix_nu2d_batch": (None, mx + [_i64p, L, _i64p]),
+        "oracle_mix_member_batch": (None, mx + [_i64p, L, _u8p]),
+        "oracle_mix_run": (I, mx + [_u8p, _u8p, L, U32, U32]),
+        "oracle_mix_run_bb": (I, mx + [_u8p, _u8p, L, U32, U32]),
+        "oracle_mix_scatter": (None, mx + [_u8p, _u8p]),
+        "oracle_mix_gather": (None, mx + [_u8p, _u8p]),
+    })
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
@@ -230,6 +242,86 @@ class Fractal:
         a = np.ascontiguousarray(np.asarray(box, dtype=np.uint8)).reshape(-1)
         out = np.zeros(self.cells, dtype=np.uint8)
         self.lib.oracle_gather(*self._fa(), _p(a, _u8p), _p(out, _u8p))
+        return out
+
+
+class MixedFractal:
+    """A fractal with a different NBB transition table at each level
+    (``tables[mu]``: k_mu x dim offsets for level mu, mu = 0 the finest),
+    common growth ratio ``s``: the combination the paper's conclusions name as
+    future work.  Compact indices are mixed-radix (level mu's digit has
+    weight k_0 ... k_(mu-1)); see ``oracle.c``."""
+
+    def __init__(self, s, r, dim, tables, lib=None):
+        assert len(tables) == r
+        self.s, self.r, self.dim = int(s), int(r), int(dim)
+        tabs = [np.asarray(t, dtype=np.int32).reshape(-1, dim) for t in tables]
+        self.ks = np.ascontiguousarray(np.array([len(t) for t in tabs] or [1], dtype=np.int32))
+        self.offs = np.ascontiguousarray(np.concatenate([t.reshape(-1) for t in tabs]) if tabs
+                                         else np.zeros(1, dtype=np.int32))
+        self.lib = lib or load()
+        self.cells = int(np.prod([len(t) for t in tabs])) if tabs else 1
+        self.side = self.s ** self.r
+        self.box_cells = self.side ** self.dim
+
+    def _fa(self):
+        return (self.s, self.r, self.dim, _p(self.ks, _i32p), _p(self.offs, _i32p))
+
+    def member(self, coords) -> np.ndarray:
+        c = np.ascontiguousarray(np.asarray(coords, dtype=np.int64).reshape(-1, self.dim))
+        m = np.zeros(len(c), dtype=np.uint8)
+        self.lib.oracle_mix_member_batch(*self._fa(), _p(c, _i64p), len(c), _p(m, _u8p))
+        return m
+
+    def lam(self, omega) -> np.ndarray:
+        w = np.ascontiguousarray(np.asarray(omega, dtype=np.int64).reshape(-1))
+        out = np.zeros((len(w), self.dim), dtype=np.int64)
+        self.lib.oracle_mix_lambda_batch(*self._fa(), _p(w, _i64p), len(w), _p(out, _i64p))
+        return out
+
+    def nu(self, coords) -> np.ndarray:
+        c = np.ascontiguousarray(np.asarray(coords, dtype=np.int64).reshape(-1, self.dim))
+        out = np.zeros(len(c), dtype=np.int64)
+        self.lib.oracle_mix_nu_batch(*self._fa(), _p(c, _i64p), len(c), _p(out, _i64p))
+        return out
+
+    def nu2d(self, coords) -> np.ndarray:
+        c = np.ascontiguousarray(np.asarray(coords, dtype=np.int64).reshape(-1, self.dim))
+        out = np.zeros((len(c), self.dim), dtype=np.int64)
+        self.lib.oracle_mix_nu2d_batch(*self._fa(), _p(c, _i64p), len(c), _p(out, _i64p))
+        return out
+
+    def init_bernoulli(self, seed: int, p: float) -> np.ndarray:
+        st = np.zeros(self.cells, dtype=np.uint8)
+        self.lib.oracle_init_bernoulli(seed & (2**64 - 1), float(p), _p(st, _u8p), 0, self.cells)
+        return st
+
+    def step(self, state, rule=LIFE, steps: int = 1) -> np.ndarray:
+        a = np.ascontiguousarray(np.asarray(state, dtype=np.uint8))
+        assert a.size == self.cells
+        out = np.zeros_like(a)
+        assert self.lib.oracle_mix_run(*self._fa(), _p(a, _u8p), _p(out, _u8p), steps,
+                                       rule.birth, rule.survive) == 0
+        return out
+
+    def bb_step(self, box, rule=LIFE, steps: int = 1) -> np.ndarray:
+        a = np.ascontiguousarray(np.asarray(box, dtype=np.uint8)).reshape(-1)
+        assert a.size == self.box_cells
+        out = np.zeros_like(a)
+        assert self.lib.oracle_mix_run_bb(*self._fa(), _p(a, _u8p), _p(out, _u8p), steps,
+                                          rule.birth, rule.survive) == 0
+        return out
+
+    def scatter(self, compact) -> np.ndarray:
+        a = np.ascontiguousarray(np.asarray(compact, dtype=np.uint8))
+        box = np.zeros(self.box_cells, dtype=np.uint8)
+        self.lib.oracle_mix_scatter(*self._fa(), _p(a, _u8p), _p(box, _u8p))
+        return box
+
+    def gather(self, box) -> np.ndarray:
+        a = np.ascontiguousarray(np.asarray(box, dtype=np.uint8)).reshape(-1)
+        out = np.zeros(self.cells, dtype=np.uint8)
+        self.lib.oracle_mix_gather(*self._fa(), _p(a, _u8p), _p(out, _u8p))
         return out
 
 

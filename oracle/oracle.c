@@ -37,6 +37,10 @@
  *   - bounding-box step (Sec. 4, approach "BB"): the same rule applied to the
  *     whole n^dim byte box (x fastest, then y, then z).  Cells off the fractal
  *     count as dead whatever their byte, and are written as 0.
+ *   - a fractal with a different transition table at each level (the
+ *     paper's conclusions, future work): the same definitions level by
+ *     level with level mu's own table, compact indices in mixed radix
+ *     (oracle_mix_*).
  *   - Bernoulli initial state: the omega-th output of SplitMix64 (Steele, Lea
  *     & Flood 2014) seeded with `seed`, i.e. mix(seed + (omega+1) * gamma);
  *     alive iff its top 53 bits are below floor(p * 2^53).  Not part of the
@@ -474,4 +478,252 @@ void oracle_init_bernoulli(uint64_t seed, double p, uint8_t *state,
     #pragma omp parallel for schedule(static)
     for (int64_t w = w0; w < w1; ++w)
         state[w] = (oracle_splitmix64_nth(seed, (uint64_t)w) >> 11) < thr;
+}
+
+/* ------------------------------------------- different tables per level */
+
+/* A fractal combined from a different NBB transition table at each scale
+ * level (the construction the paper's conclusions propose as future work):
+ * level mu (mu = 0 the finest) has ks[mu] replicas whose offsets are the
+ * ks[mu] x dim rows starting at offs + dim * (ks[0] + ... + ks[mu-1]); the
+ * growth ratio s and the dimension are common to all levels.  The cells
+ * number prod_mu ks[mu]; a compact index is the mixed-radix number
+ * omega = sum_mu d_mu * (ks[0] * ... * ks[mu-1]), d_mu the replica ID at
+ * level mu.  With the same table at every level this is the fractal above. */
+
+static const int32_t *mix_table(int dim, const int32_t *ks, const int32_t *offs, int mu)
+{
+    int64_t base = 0;
+    for (int nu = 0; nu < mu; ++nu) base += ks[nu];
+    return offs + dim * base;
+}
+
+int64_t oracle_mix_cells(int r, const int32_t *ks)
+{
+    int64_t v = 1;
+    for (int mu = 0; mu < r; ++mu) v *= ks[mu];
+    return v;
+}
+
+int oracle_mix_is_member(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                         const int64_t *p)
+{
+    if (!in_box(s, r, dim, p)) return 0;
+    for (int mu = 0; mu < r; ++mu) {
+        int64_t smu = oracle_ipow(s, mu);
+        int64_t t[OR_MAXDIM];
+        for (int i = 0; i < dim; ++i) t[i] = (p[i] / smu) % s;
+        if (replica_id(ks[mu], dim, mix_table(dim, ks, offs, mu), t) < 0) return 0;
+    }
+    return 1;
+}
+
+void oracle_mix_lambda(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                       int64_t omega, int64_t *p)
+{
+    for (int i = 0; i < dim; ++i) p[i] = 0;
+    int64_t weight = 1;   /* ks[0] * ... * ks[mu-1] */
+    for (int mu = 0; mu < r; ++mu) {
+        int64_t d = (omega / weight) % ks[mu];
+        const int32_t *off = mix_table(dim, ks, offs, mu);
+        int64_t smu = oracle_ipow(s, mu);
+        for (int i = 0; i < dim; ++i) p[i] += smu * off[d * dim + i];
+        weight *= ks[mu];
+    }
+}
+
+int64_t oracle_mix_nu(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                      const int64_t *p)
+{
+    if (!in_box(s, r, dim, p)) return -1;
+    int64_t omega = 0, weight = 1;
+    for (int mu = 0; mu < r; ++mu) {
+        int64_t smu = oracle_ipow(s, mu);
+        int64_t t[OR_MAXDIM];
+        for (int i = 0; i < dim; ++i) t[i] = (p[i] / smu) % s;
+        int h = replica_id(ks[mu], dim, mix_table(dim, ks, offs, mu), t);
+        if (h < 0) return -1;
+        omega += (int64_t)h * weight;
+        weight *= ks[mu];
+    }
+    return omega;
+}
+
+/* The compact coordinate of Eqs. 6-8 for per-level tables: level mu adds
+ * H_mu times the product of ks[nu] over the earlier levels nu of the same
+ * axis (nu < mu, nu = mu mod dim) to axis mu mod dim. */
+int oracle_mix_nu2d(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                    const int64_t *p, int64_t *c)
+{
+    int64_t weight[OR_MAXDIM];
+    for (int i = 0; i < dim; ++i) {
+        c[i] = 0;
+        weight[i] = 1;
+    }
+    if (!in_box(s, r, dim, p)) {
+        for (int i = 0; i < dim; ++i) c[i] = -1;
+        return -1;
+    }
+    for (int mu = 0; mu < r; ++mu) {
+        int64_t smu = oracle_ipow(s, mu);
+        int64_t t[OR_MAXDIM];
+        for (int i = 0; i < dim; ++i) t[i] = (p[i] / smu) % s;
+        int h = replica_id(ks[mu], dim, mix_table(dim, ks, offs, mu), t);
+        if (h < 0) {
+            for (int i = 0; i < dim; ++i) c[i] = -1;
+            return -1;
+        }
+        int axis = mu % dim;
+        c[axis] += (int64_t)h * weight[axis];
+        weight[axis] *= ks[mu];
+    }
+    return 0;
+}
+
+void oracle_mix_lambda_batch(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                             const int64_t *omega, int64_t count, int64_t *coords)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < count; ++e)
+        oracle_mix_lambda(s, r, dim, ks, offs, omega[e], coords + e * dim);
+}
+
+void oracle_mix_nu_batch(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                         const int64_t *coords, int64_t count, int64_t *omega)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < count; ++e)
+        omega[e] = oracle_mix_nu(s, r, dim, ks, offs, coords + e * dim);
+}
+
+void oracle_mix_nu2d_batch(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                           const int64_t *coords, int64_t count, int64_t *c)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < count; ++e)
+        oracle_mix_nu2d(s, r, dim, ks, offs, coords + e * dim, c + e * dim);
+}
+
+void oracle_mix_member_batch(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                             const int64_t *coords, int64_t count, uint8_t *m)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < count; ++e)
+        m[e] = (uint8_t)oracle_mix_is_member(s, r, dim, ks, offs, coords + e * dim);
+}
+
+/* One synchronous generation of the compact state (Sec. 3 stencil procedure
+ * through the per-level lambda and nu). */
+void oracle_mix_step(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                     const uint8_t *in, uint8_t *out, uint32_t birth, uint32_t survive)
+{
+    int64_t V = oracle_mix_cells(r, ks);
+    #pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t w = 0; w < V; ++w) {
+        int64_t p[OR_MAXDIM], q[OR_MAXDIM], delta[OR_MAXDIM];
+        oracle_mix_lambda(s, r, dim, ks, offs, w, p);
+        int nq = 1;
+        for (int i = 0; i < dim; ++i) nq *= 3;
+        int count = 0;
+        for (int e = 0; e < nq; ++e) {
+            moore_offset(dim, e, delta);
+            if (is_zero_offset(dim, delta)) continue;
+            for (int i = 0; i < dim; ++i) q[i] = p[i] + delta[i];
+            int64_t n = oracle_mix_nu(s, r, dim, ks, offs, q);
+            if (n >= 0 && in[n] != 0) ++count;
+        }
+        out[w] = life_rule(in[w] != 0, count, birth, survive);
+    }
+}
+
+/* One generation on the whole box with the per-level membership (cells off
+ * the fractal are dead and written 0). */
+void oracle_mix_step_bb(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                        const uint8_t *box, uint8_t *out, uint32_t birth, uint32_t survive)
+{
+    int64_t n = oracle_ipow(s, r), N = oracle_ipow(n, dim);
+    #pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t idx = 0; idx < N; ++idx) {
+        int64_t p[OR_MAXDIM], q[OR_MAXDIM], delta[OR_MAXDIM];
+        box_coords(n, dim, idx, p);
+        if (!oracle_mix_is_member(s, r, dim, ks, offs, p)) {
+            out[idx] = 0;
+            continue;
+        }
+        int nq = 1;
+        for (int i = 0; i < dim; ++i) nq *= 3;
+        int count = 0;
+        for (int e = 0; e < nq; ++e) {
+            moore_offset(dim, e, delta);
+            if (is_zero_offset(dim, delta)) continue;
+            for (int i = 0; i < dim; ++i) q[i] = p[i] + delta[i];
+            if (!oracle_mix_is_member(s, r, dim, ks, offs, q)) continue;
+            if (box[box_index(n, dim, q)] != 0) ++count;
+        }
+        out[idx] = life_rule(box[idx] != 0, count, birth, survive);
+    }
+}
+
+static int mix_run(int bb, int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                   const uint8_t *in, uint8_t *out, int64_t steps, uint32_t birth, uint32_t survive)
+{
+    int64_t V = bb ? oracle_ipow(oracle_ipow(s, r), dim) : oracle_mix_cells(r, ks);
+    uint8_t *a = (uint8_t *)malloc((size_t)V);
+    uint8_t *b = (uint8_t *)malloc((size_t)V);
+    if (!a || !b) { free(a); free(b); return -1; }
+    for (int64_t w = 0; w < V; ++w) a[w] = in[w] != 0;
+    if (bb) {
+        /* zero generations still mask the box */
+        int64_t n = oracle_ipow(s, r);
+        for (int64_t idx = 0; idx < V; ++idx) {
+            int64_t p[OR_MAXDIM];
+            box_coords(n, dim, idx, p);
+            if (!oracle_mix_is_member(s, r, dim, ks, offs, p)) a[idx] = 0;
+        }
+    }
+    for (int64_t t = 0; t < steps; ++t) {
+        if (bb) oracle_mix_step_bb(s, r, dim, ks, offs, a, b, birth, survive);
+        else oracle_mix_step(s, r, dim, ks, offs, a, b, birth, survive);
+        uint8_t *x = a; a = b; b = x;
+    }
+    memcpy(out, a, (size_t)V);
+    free(a);
+    free(b);
+    return 0;
+}
+
+int oracle_mix_run(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                   const uint8_t *in, uint8_t *out, int64_t steps, uint32_t birth, uint32_t survive)
+{
+    return mix_run(0, s, r, dim, ks, offs, in, out, steps, birth, survive);
+}
+
+int oracle_mix_run_bb(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                      const uint8_t *in, uint8_t *out, int64_t steps, uint32_t birth, uint32_t survive)
+{
+    return mix_run(1, s, r, dim, ks, offs, in, out, steps, birth, survive);
+}
+
+/* box[lambda(omega)] = compact[omega] != 0, 0 off the fractal; and back. */
+void oracle_mix_scatter(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                        const uint8_t *compact, uint8_t *box)
+{
+    int64_t n = oracle_ipow(s, r), V = oracle_mix_cells(r, ks);
+    memset(box, 0, (size_t)oracle_ipow(n, dim));
+    for (int64_t w = 0; w < V; ++w) {
+        int64_t p[OR_MAXDIM];
+        oracle_mix_lambda(s, r, dim, ks, offs, w, p);
+        box[box_index(n, dim, p)] = compact[w] != 0;
+    }
+}
+
+void oracle_mix_gather(int s, int r, int dim, const int32_t *ks, const int32_t *offs,
+                       const uint8_t *box, uint8_t *compact)
+{
+    int64_t n = oracle_ipow(s, r), V = oracle_mix_cells(r, ks);
+    for (int64_t w = 0; w < V; ++w) {
+        int64_t p[OR_MAXDIM];
+        oracle_mix_lambda(s, r, dim, ks, offs, w, p);
+        compact[w] = box[box_index(n, dim, p)] != 0;
+    }
 }
