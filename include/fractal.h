@@ -79,6 +79,22 @@ const char *fractal_version(void);
 int fractal_create(int k, int s, int r, int dim, const int32_t *offsets,
                    fractal_t **out);
 
+/* A fractal combined from a different NBB transition table at each scale
+ * level (the combination the paper's conclusions propose as future work).
+ * Level mu (mu = 0 the finest, mu < r) has ks[mu] replicas, 1 <= ks[mu] <=
+ * s^dim, whose offsets are the ks[mu] rows of dim int32 values in [0,s)
+ * that follow the rows of levels 0 .. mu-1 in `offsets`; s and dim are
+ * common.  It has prod ks[mu] cells; the compact index is the mixed-radix
+ * number omega = sum_mu d_mu (ks[0] ... ks[mu-1]) of the replica IDs, and
+ * the compact coordinate (fractal_nu2d) gives level mu's ID the weight
+ * prod ks[nu] over the earlier levels nu of the same axis (nu = mu mod dim).
+ * Supported by every call on handles except the tensor-core maps, the
+ * paper's approaches, the sharded step and temporal blocking (FR_EINVAL);
+ * the step uses the generic per-cell policy (2D) or the box policy (3D).
+ * Errors as fractal_create; r in [1, 62]. */
+int fractal_create_mixed(int s, int r, int dim, const int32_t *ks, const int32_t *offsets,
+                         fractal_t **out);
+
 /* Free a handle and the device memory it owns (tables, scratch).  Waits for
  * the handle's outstanding work.  NULL is accepted. */
 int fractal_destroy(fractal_t *f);

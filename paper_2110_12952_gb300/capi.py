@@ -35,6 +35,7 @@ SIGNATURES = {
     "fractal_last_error": (ctypes.c_char_p, []),
     "fractal_version": (ctypes.c_char_p, []),
     "fractal_create": (c_int, [c_int, c_int, c_int, c_int, c_i32p, ctypes.POINTER(c_fp)]),
+    "fractal_create_mixed": (c_int, [c_int, c_int, c_int, c_i32p, c_i32p, ctypes.POINTER(c_fp)]),
     "fractal_destroy": (c_int, [c_fp]),
     "fractal_info": (c_int, [c_fp, c_i64p, c_i64p]),
     "fractal_lambda": (c_int, [c_fp, c_vp, c_i64, c_vp, c_vp]),

@@ -145,6 +145,89 @@ extern "C" int fractal_create(int k, int s, int r, int dim, const int32_t *offse
     return FR_OK;
 }
 
+extern "C" int fractal_create_mixed(int s, int r, int dim, const int32_t *ks, const int32_t *offsets,
+                                    fractal_t **out)
+{
+    g_err.clear();
+    if (!out) return fail(FR_EINVAL, "fractal_create_mixed: out is NULL");
+    *out = nullptr;
+    if (!offsets || (!ks && r > 0)) return fail(FR_EINVAL, "fractal_create_mixed: NULL table");
+    if (dim != 2 && dim != 3) return fail(FR_EINVAL, "fractal_create_mixed: dim must be 2 or 3");
+    if (s < 2 || s > 16) return fail(FR_EINVAL, "fractal_create_mixed: s must be in [2,16]");
+    if (r < 1 || r > kMaxR) return fail(FR_EINVAL, "fractal_create_mixed: r must be in [1, 62]");
+    int sd = 1;
+    for (int i = 0; i < dim; ++i) sd *= s;
+    if (sd > kMaxSD) return fail(FR_EINVAL, "fractal_create_mixed: s^dim must be <= 256");
+    std::vector<std::vector<int16_t>> hinv(r, std::vector<int16_t>(kMaxSD, -1));
+    std::vector<int64_t> first(r);
+    int64_t rows = 0, cells = 1, side = 1;
+    for (int mu = 0; mu < r; ++mu) {
+        const int k = ks[mu];
+        if (k < 1 || k > sd) return fail(FR_EINVAL, "fractal_create_mixed: every k must be in [1, s^dim]");
+        first[mu] = rows;
+        for (int j = 0; j < k; ++j) {
+            int t = 0, m = 1;
+            for (int i = 0; i < dim; ++i) {
+                const int v = offsets[(rows + j) * dim + i];
+                if (v < 0 || v >= s) return fail(FR_EINVAL, "fractal_create_mixed: offset component outside [0,s)");
+                t += v * m;
+                m *= s;
+            }
+            if (hinv[mu][t] >= 0) return fail(FR_EINVAL, "fractal_create_mixed: duplicate offset rows in a level");
+            hinv[mu][t] = (int16_t)j;
+        }
+        rows += k;
+        if (!mul_ok(cells, k, (int64_t)1 << 62, &cells))
+            return fail(FR_EOVERFLOW, "fractal_create_mixed: the cell count reaches 2^62");
+        if (!mul_ok(side, s, ((int64_t)1 << 31) - 1, &side))
+            return fail(FR_EOVERFLOW, "fractal_create_mixed: s^r >= 2^31");
+    }
+    int64_t box = 1;
+    for (int i = 0; i < dim; ++i)
+        if (!mul_ok(box, side, INT64_MAX, &box)) { box = -1; break; }
+    fractal *f = new (std::nothrow) fractal();
+    if (!f) return fail(FR_ENOMEM, "fractal_create_mixed: out of host memory");
+    f->k = ks[0]; f->s = s; f->r = r; f->dim = dim;
+    f->offsets.assign(offsets, offsets + (size_t)rows * dim);
+    f->cells = cells;
+    f->side = side;
+    f->box_cells = box;
+    f->mixed = true;
+    f->lev_k.assign(ks, ks + r);
+    f->lev_first = first;
+    f->lev_hinv = hinv;
+    FracDev &D = f->dev;
+    memset(&D, 0, sizeof(D));
+    D.k = ks[0]; D.s = s; D.r = r; D.dim = dim; D.sd = sd;
+    D.sdiv = make_div((uint32_t)s);
+    D.kdiv = make_div((uint32_t)(ks[0] >= 2 ? ks[0] : 2));
+    for (int t = 0; t < kMaxSD; ++t) D.hinv[t] = hinv[0][t];
+    std::vector<MixLevel> lv(r);
+    for (int mu = 0; mu < r; ++mu) {
+        memset(&lv[mu], 0, sizeof(MixLevel));
+        lv[mu].k = ks[mu];
+        lv[mu].kdiv = make_div((uint32_t)(ks[mu] >= 2 ? ks[mu] : 2));
+        for (int t = 0; t < kMaxSD; ++t) lv[mu].hinv[t] = hinv[mu][t];
+        for (int j = 0; j < ks[mu]; ++j)
+            for (int i = 0; i < dim; ++i) lv[mu].off[j][i] = (int8_t)offsets[(first[mu] + j) * dim + i];
+    }
+    for (int j = 0; j < ks[0]; ++j)
+        for (int i = 0; i < dim; ++i) D.off[j][i] = lv[0].off[j][i];
+    cudaError_t e = cudaGetDevice(&f->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, f->device);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_mix, sizeof(MixLevel) * (size_t)r);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_mix, lv.data(), sizeof(MixLevel) * (size_t)r, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(f->d_mix);
+        delete f;
+        return cuda_fail(e, "fractal_create_mixed: no usable CUDA device");
+    }
+    D.mix = f->d_mix;
+    f->tile_levels_user = cached_tile_levels(f, &f->stages_user);
+    *out = f;
+    return FR_OK;
+}
+
 extern "C" int fractal_destroy(fractal_t *f)
 {
     g_err.clear();
@@ -159,6 +242,7 @@ extern "C" int fractal_destroy(fractal_t *f)
     cudaFree(f->host_io[0]);
     cudaFree(f->host_io[1]);
     cudaFree(f->status);
+    cudaFree(f->d_mix);
     delete f;
     return FR_OK;
 }

@@ -29,26 +29,27 @@ static int64_t ipow64(int64_t b, int e)
     return v;
 }
 
-// membership of a cell of the level-`levels` fractal (host, digits by hand)
-static bool host_member(const fractal *f, int64_t x, int64_t y, int64_t z, int levels)
+// membership of a cell of the fractal made of levels base .. base +
+// levels - 1 (host, digits by hand)
+static bool host_member(const fractal *f, int64_t x, int64_t y, int64_t z, int levels, int base)
 {
     for (int mu = 0; mu < levels; ++mu) {
         int t = (int)(x % f->s) + f->s * (int)(y % f->s);
         if (f->dim == 3) t += f->s * f->s * (int)(z % f->s);
         x /= f->s; y /= f->s; z /= f->s;
-        if (f->dev.hinv[t] < 0) return false;
+        if ((f->mixed ? f->lev_hinv[base + mu][t] : f->dev.hinv[t]) < 0) return false;
     }
     return true;
 }
 
-static int build_bitmap(const fractal *f, int side, int levels, uint32_t **out, int64_t *words)
+static int build_bitmap(const fractal *f, int side, int levels, int base, uint32_t **out, int64_t *words)
 {
     int64_t n = ipow64(side, f->dim);
     int64_t nw = (n + 31) / 32;
     std::vector<uint32_t> bits(nw, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t x = i % side, y = (i / side) % side, z = f->dim == 3 ? i / ((int64_t)side * side) : 0;
-        if (host_member(f, x, y, z, levels)) bits[i >> 5] |= 1u << (i & 31);
+        if (host_member(f, x, y, z, levels, base)) bits[i >> 5] |= 1u << (i & 31);
     }
     FR_CUDA(cudaMalloc(out, nw * sizeof(uint32_t)));
     FR_CUDA(cudaMemcpy(*out, bits.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -70,8 +71,8 @@ int ensure_bb_plan(fractal *f)
     p.Lb = (f->r + 1) / 2;
     p.S = (int)ipow64(f->s, p.Lb);
     p.C = (int)ipow64(f->s, f->r - p.Lb);
-    int rc = build_bitmap(f, p.S, p.Lb, &p.local_bits, &p.local_words);
-    if (!rc) rc = build_bitmap(f, p.C, f->r - p.Lb, &p.coarse_bits, &p.coarse_words);
+    int rc = build_bitmap(f, p.S, p.Lb, 0, &p.local_bits, &p.local_words);
+    if (!rc) rc = build_bitmap(f, p.C, f->r - p.Lb, p.Lb, &p.coarse_bits, &p.coarse_words);
     if (rc) {
         free_bb_plan(p);
         return rc;

@@ -106,11 +106,33 @@ struct fractal {
     int tb_levels_user = -1;         // its tile depth (-1 = automatic)
     fr::TbPlan tb;
     void *paper_aux = nullptr;       // the paper's approaches (paper_kernels.cu): geometry and scratch
+    // a different transition table per level (fractal_create_mixed); then
+    // `offsets` holds the levels' tables one after the other
+    bool mixed = false;
+    std::vector<int32_t> lev_k;              // replica count of each level
+    std::vector<int64_t> lev_first;          // first offset row of each level's table
+    std::vector<std::vector<int16_t>> lev_hinv;   // digit tuple -> replica, per level
+    fr::MixLevel *d_mix = nullptr;           // the same in device memory
     uint32_t test_extra_tx = 0;      // fractal_test_arm_timeout: next step launch's extra armed bytes
     uint32_t test_wait_limit = 0;    // ... and its wait limit (tries)
 };
 
 namespace fr {
+
+// cells of a level-L subtree (product of the replica counts of levels
+// 0 .. L-1) and subtrees of level L (levels L .. r-1)
+inline int64_t cells_below(const fractal *f, int L)
+{
+    int64_t v = 1;
+    for (int mu = 0; mu < L; ++mu) v *= f->mixed ? f->lev_k[mu] : f->k;
+    return v;
+}
+inline int64_t cells_above(const fractal *f, int L)
+{
+    int64_t v = 1;
+    for (int mu = L; mu < f->r; ++mu) v *= f->mixed ? f->lev_k[mu] : f->k;
+    return v;
+}
 
 int ensure_step_plan(fractal *f);
 int ensure_tb_plan(fractal *f);

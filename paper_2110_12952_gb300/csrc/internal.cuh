@@ -48,6 +48,15 @@ __device__ __forceinline__ uint32_t divu(const DivU32 &D, uint32_t x)
     return __umulhi(x, D.m) >> D.sh;
 }
 
+// One level of a fractal with a different transition table per level
+// (fractal_create_mixed): its replica count, division by it, and its table.
+struct MixLevel {
+    int32_t k;
+    DivU32 kdiv;
+    int16_t hinv[kMaxSD];
+    int8_t off[kMaxSD][3];
+};
+
 struct FracDev {
     int32_t k, s, r, dim;
     int32_t sd;          // s^dim
@@ -55,15 +64,48 @@ struct FracDev {
     DivU32 kdiv;         // division by k (k >= 2; unused when k == 1)
     int16_t hinv[kMaxSD];  // tuple index t0 + s*t1 + s*s*t2 -> replica id, -1 = none
     int8_t off[kMaxSD][3]; // replica id -> digit tuple
+    const MixLevel *mix;   // per-level tables in device memory (r entries), or null: every level as above
 };
+
+// digit of omega at a level with k replicas, and omega / k
+__device__ __forceinline__ uint32_t mix_digit(const MixLevel &M, uint64_t &omega)
+{
+    if (omega < (1ull << 31)) {
+        const uint32_t q = M.k > 1 ? divu(M.kdiv, (uint32_t)omega) : (uint32_t)omega;
+        const uint32_t d = (uint32_t)omega - q * (uint32_t)M.k;
+        omega = q;
+        return d;
+    }
+    const uint64_t q = omega / (uint64_t)M.k;
+    const uint32_t d = (uint32_t)(omega - q * (uint64_t)M.k);
+    omega = q;
+    return d;
+}
+
+// lambda over levels base .. base + levels - 1 of a fractal with per-level
+// tables (coordinates in units of s^base)
+__device__ __forceinline__ void lambda_mix(const FracDev &F, uint64_t omega, int levels, int base, int32_t p[3])
+{
+    int32_t px = 0, py = 0, pz = 0, sm = 1;
+    for (int mu = 0; mu < levels; ++mu) {
+        const MixLevel &M = F.mix[base + mu];
+        const uint32_t d = mix_digit(M, omega);
+        px += sm * M.off[d][0];
+        py += sm * M.off[d][1];
+        pz += sm * M.off[d][2];
+        sm *= F.s;
+    }
+    p[0] = px; p[1] = py; p[2] = pz;
+}
 
 // ------------------------------------------------------------ device maps
 
 // lambda over the lowest `levels` levels of `omega` (Sec. 3): coordinates
 // p_i = sum_mu s^mu off[d_mu][i].  Requires omega < 2^31 (fast path).
 __device__ __forceinline__ void lambda32(const FracDev &F, uint32_t omega, int levels,
-                                         int32_t p[3])
+                                         int32_t p[3], int base = 0)
 {
+    if (F.mix) return lambda_mix(F, omega, levels, base, p);
     int32_t px = 0, py = 0, pz = 0, sm = 1;
     for (int mu = 0; mu < levels; ++mu) {
         uint32_t q = (F.k > 1) ? divu(F.kdiv, omega) : omega;
@@ -77,10 +119,12 @@ __device__ __forceinline__ void lambda32(const FracDev &F, uint32_t omega, int l
     p[0] = px; p[1] = py; p[2] = pz;
 }
 
-// General lambda for 64-bit omega.
+// General lambda for 64-bit omega (levels base .. base + levels - 1; the
+// base matters only for per-level tables).
 __device__ __forceinline__ void lambda64(const FracDev &F, uint64_t omega, int levels,
-                                         int32_t p[3])
+                                         int32_t p[3], int base = 0)
 {
+    if (F.mix) return lambda_mix(F, omega, levels, base, p);
     int32_t px = 0, py = 0, pz = 0, sm = 1;
     int mu = 0;
     for (; mu < levels && omega >= (1ull << 31); ++mu) {
@@ -103,9 +147,29 @@ __device__ __forceinline__ void lambda64(const FracDev &F, uint64_t omega, int l
 // coordinates already known to lie in [0, s^levels)), or -1 if some level's
 // digit tuple is not a replica.
 __device__ __forceinline__ int64_t nu_levels(const FracDev &F, uint32_t x, uint32_t y,
-                                             uint32_t z, int levels)
+                                             uint32_t z, int levels, int base = 0)
 {
     int64_t omega = 0, km = 1;
+    if (F.mix) {
+        // per-level tables: level base + mu's inverse table and replica count
+        for (int mu = 0; mu < levels; ++mu) {
+            const MixLevel &M = F.mix[base + mu];
+            const uint32_t qx = divu(F.sdiv, x), qy = divu(F.sdiv, y);
+            uint32_t t = (x - qx * F.s) + (uint32_t)F.s * (y - qy * F.s);
+            x = qx;
+            y = qy;
+            if (F.dim == 3) {
+                const uint32_t qz = divu(F.sdiv, z);
+                t += (uint32_t)(F.s * F.s) * (z - qz * F.s);
+                z = qz;
+            }
+            const int h = M.hinv[t];
+            if (h < 0) return -1;
+            omega += (int64_t)h * km;
+            km *= M.k;
+        }
+        return omega;
+    }
     for (int mu = 0; mu < levels; ++mu) {
         uint32_t qx = divu(F.sdiv, x), qy = divu(F.sdiv, y);
         uint32_t t = (x - qx * F.s) + (uint32_t)F.s * (y - qy * F.s);

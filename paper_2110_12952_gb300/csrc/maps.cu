@@ -63,6 +63,30 @@ __global__ void nu2d_kernel(FracDev F, int32_t side, const int32_t *__restrict__
         uint32_t x = c[0], y = c[1], z = c[2];
         int64_t w = 1;
         int axis = 0;
+        if (F.mix) {
+            // per-level tables: level mu's replica ID, weighted by the replica
+            // counts of the earlier levels of the same axis
+            int64_t wa[3] = {1, 1, 1};
+            for (int mu = 0; inside && mu < F.r; ++mu) {
+                const MixLevel &M = F.mix[mu];
+                const uint32_t qx = divu(F.sdiv, x), qy = divu(F.sdiv, y);
+                uint32_t t = (x - qx * F.s) + (uint32_t)F.s * (y - qy * F.s);
+                x = qx;
+                y = qy;
+                if (F.dim == 3) {
+                    const uint32_t qz = divu(F.sdiv, z);
+                    t += (uint32_t)(F.s * F.s) * (z - qz * F.s);
+                    z = qz;
+                }
+                const int h = M.hinv[t];
+                if (h < 0) inside = false;
+                const int a = mu % F.dim;
+                acc[a] += (int64_t)h * wa[a];
+                wa[a] *= M.k;
+            }
+            for (int i = 0; i < F.dim; ++i) out[e * F.dim + i] = inside ? acc[i] : -1;
+            continue;
+        }
         for (int mu = 0; inside && mu < F.r; ++mu) {
             uint32_t qx = divu(F.sdiv, x), qy = divu(F.sdiv, y);
             uint32_t t = (x - qx * F.s) + (uint32_t)F.s * (y - qy * F.s);

@@ -270,6 +270,7 @@ static int tc_fail(const std::string &msg)
 // (per axis: limbs of k^floor(mu/dim) on the levels mu = axis mod dim)
 static int nu_plan(const fractal *f, TcPlan &P)
 {
+    if (f->mixed) return tc_fail("fractal_nu_tc: one transition table for every level only");
     memset(&P, 0, sizeof(P));
     for (int c = 0; c < kTcCols; ++c) P.out_of[c] = -1;
     if (f->r > 32) return tc_fail("fractal_nu_tc: more than 32 levels");
@@ -307,6 +308,7 @@ static int nu_plan(const fractal *f, TcPlan &P)
 // lambda: per axis, limbs of s^mu on the columns of that axis
 static int lambda_plan(const fractal *f, TcPlan &P)
 {
+    if (f->mixed) return tc_fail("fractal_lambda_tc: one transition table for every level only");
     memset(&P, 0, sizeof(P));
     for (int c = 0; c < kTcCols; ++c) P.out_of[c] = -1;
     if (f->dim * f->r > kTcMaxK) return tc_fail("fractal_lambda_tc: dim * r > 64");

@@ -259,6 +259,7 @@ void fr::fr_paper_aux_free(fractal *f)
 static int pk_prepare(fractal *f, int l, bool need_nb, PkLocal **out)
 {
     if (l < 1 || l > f->r) return pk_fail("rho_levels must be in [1, r]");
+    if (f->mixed) return pk_fail("the paper's approaches: one transition table for every level only");
     PkCache *c = pk_cache(f);
     if (c->loc.l != l) {
         pk_free(c->loc);

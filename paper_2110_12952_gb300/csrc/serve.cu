@@ -118,6 +118,7 @@ static std::string class_key(const fractal *f)
                     std::to_string(f->dim) + "," + std::to_string(f->plan.L) + "," +
                     std::to_string(f->plan.mode) + "|";
     for (int32_t v : f->offsets) k += std::to_string(v) + ",";
+    for (int32_t v : f->lev_k) k += "l" + std::to_string(v);   // per-level tables
     return k;
 }
 

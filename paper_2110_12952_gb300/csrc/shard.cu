@@ -309,7 +309,7 @@ extern "C" int fractal_shard_attach(fractal_shard_t *p, fractal_t *f)
 {
     clear_error();
     if (!p || !f) return shard_fail(FR_EINVAL, "fractal_shard_attach: NULL argument");
-    if (f->k != p->k || f->s != p->s || f->r != p->r || f->dim != p->dim || f->offsets != p->offsets)
+    if (f->mixed || f->k != p->k || f->s != p->s || f->r != p->r || f->dim != p->dim || f->offsets != p->offsets)
         return shard_fail(FR_EINVAL, "fractal_shard_attach: the handle is not the plan's fractal");
     if (f->server_refs.load() > 0)
         return shard_fail(FR_EBUSY, "fractal_shard_attach: a server still holds requests on this handle");

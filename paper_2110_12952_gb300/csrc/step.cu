@@ -107,6 +107,17 @@ static void host_lambda(const fractal *f, int64_t l, int L, int p[3])
 {
     p[0] = p[1] = p[2] = 0;
     int64_t sm = 1;
+    if (f->mixed) {
+        for (int mu = 0; mu < L; ++mu) {
+            const int k = f->lev_k[mu];
+            const int d = (int)(l % k);
+            l /= k;
+            const int32_t *off = f->offsets.data() + (f->lev_first[mu] + d) * f->dim;
+            for (int i = 0; i < f->dim; ++i) p[i] += (int)(sm * off[i]);
+            sm *= f->s;
+        }
+        return;
+    }
     for (int mu = 0; mu < L; ++mu) {
         int d = (int)(l % f->k);
         l /= f->k;
@@ -127,10 +138,10 @@ static int64_t host_nu(const fractal *f, const int q[3], int L)
             x[i] /= f->s;
             m *= f->s;
         }
-        int h = f->dev.hinv[t];
+        const int h = f->mixed ? f->lev_hinv[mu][t] : f->dev.hinv[t];
         if (h < 0) return -1;
         w += h * km;
-        km *= f->k;
+        km *= f->mixed ? f->lev_k[mu] : f->k;
     }
     return w;
 }
@@ -141,7 +152,7 @@ static int nstages() { return 3; }
 // Group mode applies to 2D fractals whose block side s^G is 3 or 4.
 static int group_levels(const fractal *f)
 {
-    if (f->dim != 2) return 0;
+    if (f->dim != 2 || f->mixed) return 0;
     if (f->s == 2) return 2;
     if (f->s == 3 || f->s == 4) return 1;
     return 0;
@@ -220,7 +231,7 @@ static_assert(unit_taps_resolved(), "every tap outside a unit's block is one of 
 
 static bool is_triangle(const fractal *f)
 {
-    if (f->dim != 2 || f->s != 2 || f->k != 3) return false;
+    if (f->mixed || f->dim != 2 || f->s != 2 || f->k != 3) return false;
     for (int i = 0; i < 6; ++i)
         if (f->offsets[i] != kTriangleOffsets[i]) return false;
     return true;
@@ -380,7 +391,7 @@ static TapTables tap_tables(const fractal *f, int L)
 // ---- rows mode: the carpet and the Vicsek fractal (see rows_layout.h)
 static int rows_preset_of(const fractal *f)
 {
-    if (f->dim != 2 || f->s != 3) return -1;
+    if (f->mixed || f->dim != 2 || f->s != 3) return -1;
     auto same = [&](int k, const int *ox, const int *oy) {
         if (f->k != k) return false;
         for (int j = 0; j < k; ++j)
@@ -719,7 +730,7 @@ static Geometry plan_geometry(const fractal *f, int L)
         g.Px = g.B + 2;
         g.Py = g.B + 2;
         g.planes = (f->dim == 3) ? g.B + 2 : 1;
-        g.tab_entries = ipow(f->k, L);
+        g.tab_entries = cells_below(f, L);
     }
     g.box_bytes = round16(g.Px * g.Py * g.planes + 16);
     return g;
@@ -739,7 +750,7 @@ static Layout plan_layout(const fractal *f, int L)
 {
     Layout y;
     Geometry g = plan_geometry(f, L);
-    int64_t KL = ipow(f->k, L);
+    int64_t KL = cells_below(f, L);
     y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1 ||
                 g.mode == kModeLid1 || g.mode == kModeBox3) ? 2 : nstages();
     if (f->stages_user >= 2) y.nstage = f->stages_user;
@@ -775,7 +786,7 @@ static int choose_levels(const fractal *f)
         if (plan_layout(f, L).total > budget) break;
         best = L;
     }
-    while (best < f->r && ipow(f->k, f->r - best) >= ((int64_t)1 << 31)) ++best;
+    while (best < f->r && cells_above(f, best) >= ((int64_t)1 << 31)) ++best;
     return best;
 }
 
@@ -796,7 +807,8 @@ __global__ void nbr_table_kernel(FracDev F, int64_t NT, int coarse_levels, int32
     for (int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; T < NT;
          T += (int64_t)gridDim.x * blockDim.x) {
         int32_t c[3];
-        lambda64(F, (uint64_t)T, coarse_levels, c);
+        const int base = F.r - coarse_levels;   // the coarse levels sit above the tile's
+        lambda64(F, (uint64_t)T, coarse_levels, c, base);
         int slot = 0;
         for (int q = 0; q < ndir; ++q) {
             int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = (F.dim == 3) ? q / 9 - 1 : 0;
@@ -805,7 +817,7 @@ __global__ void nbr_table_kernel(FracDev F, int64_t NT, int coarse_levels, int32
             int64_t t = -1;
             if (qx >= 0 && qx < coarse_side && qy >= 0 && qy < coarse_side &&
                 (F.dim == 2 || (qz >= 0 && qz < coarse_side)))
-                t = nu_levels(F, qx, qy, F.dim == 3 ? qz : 0, coarse_levels);
+                t = nu_levels(F, qx, qy, F.dim == 3 ? qz : 0, coarse_levels, base);
             table[T * nbrw + slot++] = (int32_t)t;
         }
         for (; slot < nbrw; ++slot) table[T * nbrw + slot] = -1;
@@ -856,8 +868,8 @@ int ensure_step_plan(fractal *f)
     if (rc) return rc;
     StepPlan p;
     p.L = L;
-    p.KL = ipow(f->k, L);
-    p.NT = ipow(f->k, f->r - L);
+    p.KL = cells_below(f, L);
+    p.NT = cells_above(f, L);
     p.B = (int)ipow(f->s, L);
     p.coarse_levels = f->r - L;
     if (p.NT >= ((int64_t)1 << 31)) {
@@ -2596,6 +2608,10 @@ static std::string tune_key(const fractal *f)
     std::string key = name + "|" + std::to_string(f->k) + "," + std::to_string(f->s) + "," +
                       std::to_string(f->r) + "," + std::to_string(f->dim) + "|";
     for (int32_t v : f->offsets) key += std::to_string(v) + ",";
+    if (f->mixed) {
+        key += "|levels:";
+        for (int32_t v : f->lev_k) key += std::to_string(v) + ",";
+    }
     return key;
 }
 
@@ -2625,7 +2641,7 @@ int autotune_step(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth, u
     FR_CUDA(cudaEventCreate(&e0));
     FR_CUDA(cudaEventCreate(&e1));
     for (int L = lmax; L >= 0 && L >= lmax - 3; --L) {
-        if (ipow(f->k, f->r - L) >= ((int64_t)1 << 31)) break;
+        if (cells_above(f, L) >= ((int64_t)1 << 31)) break;
         for (int ns = 2; ns <= 4; ++ns) {
             f->tile_levels_user = L;
             f->stages_user = ns;

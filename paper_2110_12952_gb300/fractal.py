@@ -51,6 +51,28 @@ class Fractal:
     def from_family(cls, fam: Family, r: int) -> "Fractal":
         return cls(fam.k, fam.s, r, fam.dim, fam.table())
 
+    @classmethod
+    def mixed(cls, s: int, dim: int, tables) -> "Fractal":
+        """``fractal_create_mixed``: level mu (mu = 0 the finest) uses
+        ``tables[mu]`` (k_mu x dim offsets); r = len(tables)."""
+        tabs = [np.asarray(t, dtype=np.int32).reshape(-1, dim) for t in tables]
+        ks = np.ascontiguousarray(np.array([len(t) for t in tabs], dtype=np.int32))
+        off = np.ascontiguousarray(np.concatenate([t.reshape(-1) for t in tabs]).astype(np.int32))
+        self = cls.__new__(cls)
+        self._lib = capi.load()
+        h = capi.c_fp()
+        capi.check(self._lib.fractal_create_mixed(s, len(tabs), dim, ks.ctypes.data_as(capi.c_i32p),
+                                                  off.ctypes.data_as(capi.c_i32p), ctypes.byref(h)), self._lib)
+        self._h = h
+        self.k, self.s, self.r, self.dim = int(ks[0]), s, len(tabs), dim
+        self.offsets = tabs[0].copy()
+        self.level_tables = [t.copy() for t in tabs]
+        cells, side = ctypes.c_int64(), ctypes.c_int64()
+        capi.check(self._lib.fractal_info(h, ctypes.byref(cells), ctypes.byref(side)), self._lib)
+        self.cells, self.side = cells.value, side.value
+        self.box_cells = self.side ** dim
+        return self
+
     # ------------------------------------------------------------ lifetime
     def close(self):
         if getattr(self, "_h", None):
