@@ -228,6 +228,8 @@ extern "C" int fractal_create_mixed(int s, int r, int dim, const int32_t *ks, co
     return FR_OK;
 }
 
+static void free_pipe(HostPipe &p);
+
 extern "C" int fractal_destroy(fractal_t *f)
 {
     g_err.clear();
@@ -243,6 +245,7 @@ extern "C" int fractal_destroy(fractal_t *f)
     cudaFree(f->host_io[1]);
     cudaFree(f->status);
     cudaFree(f->d_mix);
+    free_pipe(f->pipe);
     delete f;
     return FR_OK;
 }
@@ -438,15 +441,116 @@ extern "C" int fractal_bb_step(fractal_t *f, const uint8_t *in, uint8_t *out, in
     });
 }
 
+static void free_pipe(HostPipe &p)
+{
+    if (p.s_h2d) cudaStreamDestroy(p.s_h2d);
+    if (p.s_comp) cudaStreamDestroy(p.s_comp);
+    if (p.s_d2h) cudaStreamDestroy(p.s_d2h);
+    for (cudaEvent_t e : p.ev_in) cudaEventDestroy(e);
+    for (cudaEvent_t e : p.ev_out) cudaEventDestroy(e);
+    if (p.ev_start) cudaEventDestroy(p.ev_start);
+    if (p.ev_done) cudaEventDestroy(p.ev_done);
+    p = HostPipe();
+}
+
+// Chunks of about kPipeChunkBytes (at most 64) and their schedule, from the
+// neighbour-tile table of the current step plan.
+constexpr int64_t kPipeChunkBytes = (int64_t)32 << 20;
+
+static int ensure_pipe(fractal *f)
+{
+    HostPipe &p = f->pipe;
+    if (p.L == f->plan.L && p.NT == f->plan.NT && !p.bounds.empty()) return FR_OK;
+    free_pipe(p);
+    const int64_t NT = f->plan.NT;
+    const int C = (int)std::max<int64_t>(1, std::min<int64_t>({64, NT, f->cells / kPipeChunkBytes}));
+    p.bounds.resize(C + 1);
+    for (int c = 0; c <= C; ++c) p.bounds[c] = NT * c / C;
+    std::vector<int32_t> nbr((size_t)(NT * f->plan.nbrw));
+    FR_CUDA(cudaMemcpy(nbr.data(), f->plan.nbr, nbr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    p.need.assign(C, 0);
+    int c = 0;
+    for (int64_t T = 0; T < NT; ++T) {
+        while (T >= p.bounds[c + 1]) ++c;
+        int64_t far = T;
+        for (int d = 0; d < f->plan.nbrw; ++d) far = std::max<int64_t>(far, nbr[(size_t)(T * f->plan.nbrw + d)]);
+        const int fc = (int)(std::upper_bound(p.bounds.begin(), p.bounds.end(), far) - p.bounds.begin()) - 1;
+        p.need[c] = std::max(p.need[c], fc);
+    }
+    p.order.resize(C);
+    for (int i = 0; i < C; ++i) p.order[i] = i;
+    std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) { return p.need[a] < p.need[b]; });
+    FR_CUDA(cudaStreamCreateWithFlags(&p.s_h2d, cudaStreamNonBlocking));
+    FR_CUDA(cudaStreamCreateWithFlags(&p.s_comp, cudaStreamNonBlocking));
+    FR_CUDA(cudaStreamCreateWithFlags(&p.s_d2h, cudaStreamNonBlocking));
+    p.ev_in.assign(C, nullptr);
+    p.ev_out.assign(C, nullptr);
+    for (int i = 0; i < C; ++i) {
+        FR_CUDA(cudaEventCreateWithFlags(&p.ev_in[i], cudaEventDisableTiming));
+        FR_CUDA(cudaEventCreateWithFlags(&p.ev_out[i], cudaEventDisableTiming));
+    }
+    FR_CUDA(cudaEventCreateWithFlags(&p.ev_start, cudaEventDisableTiming));
+    FR_CUDA(cudaEventCreateWithFlags(&p.ev_done, cudaEventDisableTiming));
+    p.L = f->plan.L;
+    p.NT = NT;
+    return FR_OK;
+}
+
+// One generation from host memory to host memory, pipelined over chunks of
+// tiles: the host-to-device and device-to-host copies run at the same time
+// (the link carries both directions at once), each chunk computed as soon
+// as its inputs have landed.
+static int run_host_pipelined(fractal *f, const uint8_t *host_in, uint8_t *host_out, uint32_t birth,
+                              uint32_t survive, cudaStream_t st)
+{
+    int rc = ensure_pipe(f);
+    if (rc) return rc;
+    HostPipe &p = f->pipe;
+    const int64_t KL = f->plan.KL;
+    const int C = (int)p.need.size();
+    uint8_t *din = f->host_io[0], *dout = f->host_io[1];
+    FR_CUDA(cudaEventRecord(p.ev_start, st));
+    FR_CUDA(cudaStreamWaitEvent(p.s_h2d, p.ev_start, 0));
+    FR_CUDA(cudaStreamWaitEvent(p.s_comp, p.ev_start, 0));
+    FR_CUDA(cudaStreamWaitEvent(p.s_d2h, p.ev_start, 0));
+    for (int j = 0; j < C; ++j) {
+        const int64_t b0 = p.bounds[j] * KL, b1 = p.bounds[j + 1] * KL;
+        FR_CUDA(cudaMemcpyAsync(din + b0, host_in + b0, (size_t)(b1 - b0), cudaMemcpyHostToDevice, p.s_h2d));
+        FR_CUDA(cudaEventRecord(p.ev_in[j], p.s_h2d));
+    }
+    for (int i = 0; i < C; ++i) {
+        const int c = p.order[i];
+        FR_CUDA(cudaStreamWaitEvent(p.s_comp, p.ev_in[p.need[c]], 0));
+        rc = launch_step_range(f, din, dout, p.bounds[c], p.bounds[c + 1], birth, survive, p.s_comp);
+        if (rc) return rc;
+        FR_CUDA(cudaEventRecord(p.ev_out[c], p.s_comp));
+        FR_CUDA(cudaStreamWaitEvent(p.s_d2h, p.ev_out[c], 0));
+        const int64_t b0 = p.bounds[c] * KL, b1 = p.bounds[c + 1] * KL;
+        FR_CUDA(cudaMemcpyAsync(host_out + b0, dout + b0, (size_t)(b1 - b0), cudaMemcpyDeviceToHost, p.s_d2h));
+    }
+    FR_CUDA(cudaEventRecord(p.ev_done, p.s_d2h));
+    FR_CUDA(cudaStreamWaitEvent(st, p.ev_done, 0));
+    return FR_OK;
+}
+
 extern "C" int fractal_run_host(fractal_t *f, const uint8_t *host_in, uint8_t *host_out,
                                 int64_t steps, uint32_t birth, uint32_t survive, void *stream)
 {
     g_err.clear();
     if (!f || !host_in || !host_out) return fail(FR_EINVAL, "fractal_run_host: NULL argument");
+    if (steps < 0) return fail(FR_EINVAL, "fractal_run_host: steps < 0");
     cudaStream_t st = (cudaStream_t)stream;
     int rc = ensure_buffer(&f->host_io[0], f->cells, "fractal_run_host: device buffer");
     if (!rc) rc = ensure_buffer(&f->host_io[1], f->cells, "fractal_run_host: device buffer");
     if (rc) return rc;
+    if (steps == 1 && f->tb_gens == 0) {
+        rc = ensure_step_plan(f);
+        if (rc) return rc;
+        rc = run_host_pipelined(f, host_in, host_out, birth, survive, st);
+        if (rc) return rc;
+        FR_CUDA(cudaStreamSynchronize(st));
+        return take_status(f);
+    }
     FR_CUDA(cudaMemcpyAsync(f->host_io[0], host_in, (size_t)f->cells, cudaMemcpyHostToDevice, st));
     rc = fractal_step(f, f->host_io[0], f->host_io[1], steps, birth, survive, stream);
     if (rc) return rc;

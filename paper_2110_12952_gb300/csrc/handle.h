@@ -82,6 +82,21 @@ struct TbPlan {
     int32_t *nbr = nullptr;
 };
 
+// fractal_run_host's pipeline for one generation: the tiles in chunks
+// (omega order), each chunk computed once the chunks that hold its tiles'
+// neighbours have arrived, its results copied back while later chunks are
+// still arriving.
+struct HostPipe {
+    int L = -1;
+    int64_t NT = 0;
+    std::vector<int64_t> bounds;   // chunk c = tiles bounds[c] .. bounds[c+1] - 1
+    std::vector<int> need;         // the last input chunk chunk c reads
+    std::vector<int> order;        // chunks by need, then index
+    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_out;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+};
+
 }  // namespace fr
 
 struct fractal {
@@ -100,6 +115,7 @@ struct fractal {
     uint8_t *scratch = nullptr;      // k^r bytes, ping-pong for steps > 1
     uint8_t *bb_scratch = nullptr;   // n^dim bytes, ping-pong for BB steps > 1
     uint8_t *host_io[2] = {nullptr, nullptr};  // device buffers of run_host
+    fr::HostPipe pipe;                          // run_host's chunked pipeline
     int *status = nullptr;           // device word set by kernels whose bounded waits gave up
     std::atomic<int> server_refs{0}; // requests of a server not yet done (the plan must not change)
     int tb_gens = 0;                 // temporal blocking: generations per pass (0 = off)
@@ -149,6 +165,10 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
 // One generation of the tiles 0 .. ntiles-1 of the buffer `in` (tile T at
 // cell T k^L) with the neighbour table `nbr` (ntiles rows, indices of tiles
 // of the same buffer, which holds readable_cells cells), into `out`.
+// One generation of the instance's tiles T0 .. T1 - 1 only (the others are
+// read as neighbours, not written).
+int launch_step_range(fractal *f, const uint8_t *in, uint8_t *out, int64_t T0, int64_t T1, uint32_t birth,
+                      uint32_t survive, cudaStream_t st);
 int launch_step_tiles(fractal *f, const uint8_t *in, uint8_t *out, const int32_t *nbr, int64_t ntiles,
                       int64_t readable_cells, uint32_t birth, uint32_t survive, cudaStream_t st);
 int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,

@@ -65,6 +65,7 @@ constexpr int kRunMax = 8;     // padded units: most units per halo run
 
 struct StepArgs {
     int64_t KL, NT, cells;
+    int64_t tile0;         // single-instance launches: the first tile of the launch (tiles tile0 .. tile0 + NT - 1)
     int Px, Py;            // box row pitch and rows per plane (bytes / rows)
     int nring, nbrw, nstage, stage_bytes, tile_bytes;
     int nhalo;             // padded-unit policies: runs of halo units per tile, in `ring`
@@ -1649,7 +1650,7 @@ __device__ __forceinline__ TileRef resolve(const StepArgs &a, const uint8_t *in,
         t.out = out;
         t.nbr = a.nbr;
         t.cells = a.cells;
-        t.T = Tg;
+        t.T = a.tile0 + Tg;
     } else {
         const InstDesc *d = a.insts + __ldg(a.tile_inst + Tg);
         if (a.gen & 1) {
@@ -2277,6 +2278,7 @@ static void fill_args(const fractal *f, StepArgs &a)
     const StepPlan &p = f->plan;
     a.KL = p.KL;
     a.NT = p.NT;
+    a.tile0 = 0;
     a.cells = f->cells;
     a.Px = p.Px;
     a.Py = p.Py;
@@ -2357,6 +2359,19 @@ int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth
         f->test_wait_limit = 0;
     }
     return dispatch<false>(f, a, f->plan.grid, in, out, st);
+}
+
+int launch_step_range(fractal *f, const uint8_t *in, uint8_t *out, int64_t T0, int64_t T1, uint32_t birth,
+                      uint32_t survive, cudaStream_t st)
+{
+    if (T1 <= T0) return FR_OK;
+    StepArgs a;
+    fill_args(f, a);
+    make_rule(birth, survive, &a.rule);
+    a.tile0 = T0;
+    a.NT = T1 - T0;
+    const int grid = (int)std::min<int64_t>((int64_t)f->plan.per_sm * f->num_sms, a.NT);
+    return dispatch<false>(f, a, grid, in, out, st);
 }
 
 int launch_step_tiles(fractal *f, const uint8_t *in, uint8_t *out, const int32_t *nbr, int64_t ntiles,

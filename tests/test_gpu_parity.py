@@ -452,3 +452,25 @@ def test_errors(P):
         g.step(x[: g.cells], out=x[g.cells:], steps=-1)
     with pytest.raises(FractalError, match="EINVAL"):
         g.tile_levels = 7
+
+
+@pytest.mark.parametrize("fam,r", [(W.TRIANGLE, 17), (W.CARPET, 9), (W.VICSEK, 12)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_run_host_pipelined_chunks(P, fam, r):
+    # one generation from host memory runs in chunks of tiles whose copies
+    # overlap: the result must equal the device-resident step (checked against
+    # the oracle elsewhere), also from and to host buffers that are not
+    # 16-byte aligned
+    g = gpu_fr(P, fam, r)
+    x = g.init_bernoulli(79 + r, 0.4)
+    want = g.step(x, steps=1, rule=rule_of(fam)).cpu()
+    hbuf = torch.zeros(g.cells + 8, dtype=torch.uint8).pin_memory()
+    obuf = torch.zeros(g.cells + 8, dtype=torch.uint8).pin_memory()
+    for off in (0, 3):
+        hin, hout = hbuf[off:off + g.cells], obuf[5:5 + g.cells] if off else obuf[:g.cells]
+        hin.copy_(x.cpu())
+        hout.zero_()
+        g.run_host(hin, hout, steps=1, rule=rule_of(fam))
+        assert torch.equal(hout, want), off
+    del x, want
+    torch.cuda.empty_cache()
