@@ -715,16 +715,16 @@ def _tb_smem(L):
 
 
 def others_compare(args, W):
-    """Carpet r=10, Vicsek r=12, Menger r=6 (p 0.5, seeds 4-6; Menger B5/S45):
-    one generation per timed step after autotuning the tile depth; states
-    smaller than L2 are timed with an L2 flush before each generation.  The
-    carpet's and Menger's bounding boxes fit and are timed too."""
+    """Carpet r=10, Vicsek r=12, Menger r=6 and r=7 (p 0.5, seeds 4-7; Menger
+    B5/S45): one generation per timed step after autotuning the tile depth;
+    states smaller than L2 are timed with an L2 flush before each generation.
+    The carpet's and the Menger r=6 bounding boxes fit and are timed too."""
     import torch
     from paper_2110_12952_gb300 import Fractal
     peak, _ = measured_peak()
     flush_buf = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
     out = {}
-    for inst in (W.CARPET_R10, W.VICSEK_R12, W.MENGER_R6):
+    for inst in (W.CARPET_R10, W.VICSEK_R12, W.MENGER_R6, W.MENGER_R7):
         g = Fractal.from_family(inst.family, inst.r)
         x = g.init_bernoulli(inst.seed, inst.p)
         y = torch.empty_like(x)

@@ -1,0 +1,290 @@
+// bit3.cuh -- the "bit3" policy of the compact step for 3D fractals with
+// s = 3 and k a multiple of 4 (the Menger sponge, k = 20): one warp per
+// level-3 tile and no block barriers.  The tile's 27^3 box with its one-cell
+// halo is held bit-sliced, one 32-bit word per box row (y, z): bit x + 1 is
+// cell x, bits 0 and 28 are the halo cells.  The 27-cell totals of the
+// 26-neighbour rule (Sec. 3 stencil, in three dimensions) are carry-save
+// adders on whole rows: the x-sums of a row from two shifts and a full
+// adder, the y-sums across the warp's lanes (lane = y) by shuffles, the
+// z-sums slid down z in registers.  Included by step.cu after its helpers.
+//
+// Per tile the warp
+//   1. fetches the halo: the 112 box rows with y or z on the halo, one cell
+//      per lane and a ballot per row, then the two x-halo bits of the other
+//      729 rows, one row per lane;
+//   2. turns the tile's cells into box bits.  A level-1 block is k bytes
+//      (consecutive in omega) filling a 3x3x3 cube; four cells of a word
+//      become a nibble through a carry-free multiply, a table maps each
+//      word's nibble to its cube bits, and the cube's 3-bit row pieces are
+//      ORed into the box rows (shared-memory atomics: up to nine blocks share
+//      a row);
+//   3. replaces the inner rows by the next generation, walking down z;
+//   4. reads each block's row pieces back, a table maps them to the block's
+//      k result bits, and a multiply spreads each nibble into four bytes.
+// The tile's bytes move through a per-warp buffer of 32 blocks, so that
+// global loads and stores are whole 16-byte words.
+#pragma once
+
+#include <stdint.h>
+
+#include "bit3_layout.h"
+
+namespace fr {
+
+__device__ __forceinline__ uint32_t b3_xor3(uint32_t a, uint32_t b, uint32_t c) { return a ^ b ^ c; }
+__device__ __forceinline__ uint32_t b3_maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
+
+// A count per bit position, bit-sliced: value = b0 + 2 b1 + 4 b2 + 8 b3.
+struct B3Q {
+    uint32_t b0, b1, b2, b3;
+};
+// The same with five slices (totals <= 27).
+struct B3T {
+    uint32_t t0, t1, t2, t3, t4;
+};
+
+// Sums over x and y of the 3x3 cells around each cell of row (lane, z): the
+// row's x-sums (0..3) from its own word, added to those of rows y - 1 and
+// y + 1 (the neighbouring lanes).  Lanes 0 and 28 (halo rows) get values
+// that are never used.
+__device__ __forceinline__ B3Q b3_sxy(uint32_t w)
+{
+    const uint32_t l = w << 1, r = w >> 1;
+    const uint32_t s0 = b3_xor3(l, w, r), s1 = b3_maj3(l, w, r);
+    const uint32_t u0 = __shfl_up_sync(0xffffffffu, s0, 1), u1 = __shfl_up_sync(0xffffffffu, s1, 1);
+    const uint32_t d0 = __shfl_down_sync(0xffffffffu, s0, 1), d1 = __shfl_down_sync(0xffffffffu, s1, 1);
+    B3Q q;
+    q.b0 = b3_xor3(u0, s0, d0);
+    const uint32_t k1 = b3_maj3(u0, s0, d0);                              // weight 2
+    const uint32_t v1 = b3_xor3(u1, s1, d1), v2 = b3_maj3(u1, s1, d1);    // weights 2, 4
+    q.b1 = k1 ^ v1;
+    const uint32_t k2 = k1 & v1;                                          // weight 4
+    q.b2 = v2 ^ k2;
+    q.b3 = v2 & k2;
+    return q;
+}
+
+// a + b + c for three counts <= 9 (carry-save, ripple over the weights)
+__device__ __forceinline__ B3T b3_add3(const B3Q &a, const B3Q &b, const B3Q &c)
+{
+    B3T t;
+    t.t0 = b3_xor3(a.b0, b.b0, c.b0);
+    const uint32_t c1 = b3_maj3(a.b0, b.b0, c.b0);                              // 2
+    const uint32_t x1 = b3_xor3(a.b1, b.b1, c.b1), y2 = b3_maj3(a.b1, b.b1, c.b1);  // 2, 4
+    t.t1 = x1 ^ c1;
+    const uint32_t z2 = x1 & c1;                                                // 4
+    const uint32_t p2 = b3_xor3(a.b2, b.b2, c.b2), q3 = b3_maj3(a.b2, b.b2, c.b2);  // 4, 8
+    t.t2 = b3_xor3(p2, y2, z2);
+    const uint32_t r3 = b3_maj3(p2, y2, z2);                                    // 8
+    const uint32_t m3 = b3_xor3(a.b3, b.b3, c.b3), n4 = b3_maj3(a.b3, b.b3, c.b3);  // 8, 16
+    t.t3 = b3_xor3(m3, q3, r3);
+    t.t4 = n4 | b3_maj3(m3, q3, r3);   // one weight-16 carry at most: totals are <= 27
+    return t;
+}
+
+template <int V>
+__device__ __forceinline__ uint32_t b3_eq(const B3T &t)
+{
+    const uint32_t a = (V & 1) ? t.t0 : ~t.t0, b = (V & 2) ? t.t1 : ~t.t1, c = (V & 4) ? t.t2 : ~t.t2;
+    const uint32_t d = (V & 8) ? t.t3 : ~t.t3, e = (V & 16) ? t.t4 : ~t.t4;
+    return a & b & c & d & e;
+}
+
+// positions whose total equals v (v is the same in every lane)
+__device__ __forceinline__ uint32_t b3_eq_rt(int v, const B3T &t)
+{
+    switch (v) {
+#define FR_B3_EQ(V) case V: return b3_eq<V>(t);
+        FR_B3_EQ(0) FR_B3_EQ(1) FR_B3_EQ(2) FR_B3_EQ(3) FR_B3_EQ(4) FR_B3_EQ(5) FR_B3_EQ(6)
+        FR_B3_EQ(7) FR_B3_EQ(8) FR_B3_EQ(9) FR_B3_EQ(10) FR_B3_EQ(11) FR_B3_EQ(12) FR_B3_EQ(13)
+        FR_B3_EQ(14) FR_B3_EQ(15) FR_B3_EQ(16) FR_B3_EQ(17) FR_B3_EQ(18) FR_B3_EQ(19) FR_B3_EQ(20)
+        FR_B3_EQ(21) FR_B3_EQ(22) FR_B3_EQ(23) FR_B3_EQ(24) FR_B3_EQ(25) FR_B3_EQ(26) FR_B3_EQ(27)
+#undef FR_B3_EQ
+        default: return 0u;
+    }
+}
+
+// The life-like rule on totals that count the cell itself: a dead cell is
+// born at a total in `bonly` or `both`, a live cell survives at one in
+// `sonly` or `both` (masks of totals 0..27).
+__device__ __forceinline__ uint32_t b3_rule(const B3T &t, uint32_t alive, uint32_t both, uint32_t sonly,
+                                            uint32_t bonly)
+{
+    uint32_t e = 0u, es = 0u, eb = 0u;
+    for (uint32_t m = both; m; m &= m - 1) e |= b3_eq_rt(__ffs(m) - 1, t);
+    for (uint32_t m = sonly; m; m &= m - 1) es |= b3_eq_rt(__ffs(m) - 1, t);
+    for (uint32_t m = bonly; m; m &= m - 1) eb |= b3_eq_rt(__ffs(m) - 1, t);
+    return e | (alive & es) | (~alive & eb);
+}
+
+// Copy n bytes (a multiple of 4) between global memory and the warp's
+// buffer: 16-byte words when the global side allows, else 4-byte words or
+// bytes.
+__device__ __forceinline__ void b3_copy_in(uint8_t *dst, const uint8_t *src, int n, int lane)
+{
+    if ((((uintptr_t)src) & 15) == 0 && (n & 15) == 0) {
+        for (int i = lane; i < n / 16; i += 32)
+            reinterpret_cast<uint4 *>(dst)[i] = __ldg(reinterpret_cast<const uint4 *>(src) + i);
+    } else if ((((uintptr_t)src) & 3) == 0) {
+        for (int i = lane; i < n / 4; i += 32)
+            reinterpret_cast<uint32_t *>(dst)[i] = __ldg(reinterpret_cast<const uint32_t *>(src) + i);
+    } else {
+        for (int i = lane; i < n; i += 32) dst[i] = __ldg(src + i);
+    }
+}
+
+__device__ __forceinline__ void b3_copy_out(uint8_t *dst, const uint8_t *src, int n, int lane)
+{
+    if ((((uintptr_t)dst) & 15) == 0 && (n & 15) == 0) {
+        for (int i = lane; i < n / 16; i += 32)
+            reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+    } else if ((((uintptr_t)dst) & 3) == 0) {
+        for (int i = lane; i < n / 4; i += 32)
+            reinterpret_cast<uint32_t *>(dst)[i] = reinterpret_cast<const uint32_t *>(src)[i];
+    } else {
+        for (int i = lane; i < n; i += 32) dst[i] = src[i];
+    }
+}
+
+// B5S45: the rule is B5/S45 (totals 5 for birth, 5 and 6 for survival),
+// evaluated with constants; otherwise the rule of the tile's instance.
+template <bool MULTI, bool B5S45>
+__global__ void __launch_bounds__(32 * kB3Warps, 4)
+step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *stab = reinterpret_cast<uint32_t *>(smem);
+    for (int i = threadIdx.x; i < a.b3.nshared; i += blockDim.x) stab[i] = __ldg(a.tab + i);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *box = reinterpret_cast<uint32_t *>(smem + a.b3.off_warp + warp * kB3WarpBytes);
+    uint8_t *io = reinterpret_cast<uint8_t *>(box + kB3BoxWords);
+    const uint32_t *CT = stab, *RT = stab + a.b3.off_rt, *BP = stab + a.b3.off_bp;
+    const uint32_t *tabx = a.tab + a.b3.off_x, *tabf = a.tab + a.b3.off_full;
+    const int k = a.b3.k, kw = k / 4, nblk = k * k;
+    const int64_t KL = a.KL;
+    const uint32_t rowset = a.b3.rowset;
+
+    for (int64_t Tg = (int64_t)blockIdx.x * kB3Warps + warp; Tg < a.NT; Tg += (int64_t)gridDim.x * kB3Warps) {
+        const TileRef t = resolve<MULTI>(a, in, out, Tg);
+        Rule rule;
+        tile_rule<MULTI>(a, Tg, rule);
+        const uint32_t mb = rule.birth & 0x7ffffffu, ms = (rule.survive << 1) & 0xffffffeu;
+        const uint32_t both = mb & ms, sonly = ms & ~mb, bonly = mb & ~ms;
+        const int32_t nb = lane < 26 ? __ldg(t.nbr + t.T * a.nbrw + lane) : -1;
+        const uint8_t *src = t.in;
+        const uint8_t *tin = t.in + t.T * KL;
+        uint8_t *tout = t.out + t.T * KL;
+
+        // 1. the halo.  Rows with y or z on the halo: lane x holds cell
+        // x - 1 of the row (entry: neighbour slot << 16 | its local omega)
+        for (int i0 = 0; i0 < kB3FullRows; i0 += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t e = __ldg(tabf + (i0 + j) * 32 + lane);
+                const int32_t tn = __shfl_sync(0xffffffffu, nb, (int)(e >> 16) & 31);
+                v[j] = 0u;
+                if (e != 0xffffffffu && tn >= 0) v[j] = __ldg(src + (int64_t)tn * KL + (e & 0xffffu));
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t w = __ballot_sync(0xffffffffu, v[j] != 0u) & 0x1fffffffu;
+                if (lane == j) box[b3_full_row(i0 + j)] = w;
+            }
+        }
+        // inner rows: cell -1 from the -x tile (slot 12), cell 27 from the
+        // +x tile (slot 13); the tile's own cells are ORed in below
+        {
+            const int32_t tl = __shfl_sync(0xffffffffu, nb, 12), tr = __shfl_sync(0xffffffffu, nb, 13);
+#pragma unroll 4
+            for (int i = lane; i < kB3Inner; i += 32) {
+                const uint32_t e = __ldg(tabx + i);
+                const uint32_t lo = e & 0xffffu, hi = e >> 16;
+                uint32_t w = 0u;
+                if (tl >= 0 && lo != 0xffffu) w = __ldg(src + (int64_t)tl * KL + lo) != 0;
+                if (tr >= 0 && hi != 0xffffu) w |= (uint32_t)(__ldg(src + (int64_t)tr * KL + hi) != 0) << 28;
+                const int z = i / 27;
+                box[(1 + i - 27 * z) + kB3Pitch * (1 + z)] = w;
+            }
+        }
+        __syncwarp();
+
+        // 2. the tile's cells, 32 blocks at a time
+        for (int j0 = 0; j0 < nblk; j0 += 32) {
+            const int nhere = min(32, nblk - j0);
+            b3_copy_in(io, tin + (int64_t)k * j0, k * nhere, lane);
+            __syncwarp();
+            if (lane < nhere) {
+                const uint32_t *wp = reinterpret_cast<const uint32_t *>(io + k * lane);
+                uint32_t cube = 0u;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    if (q < kw) {
+                        const uint32_t w = wp[q];
+                        const uint32_t c = (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;  // bit 7 of a nonzero byte
+                        cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];                            // bits 7,15,23,31 -> 28..31
+                    }
+                }
+                const uint32_t bp = BP[j0 + lane];
+                const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
+#pragma unroll
+                for (int rr = 0; rr < 9; ++rr) {
+                    if ((rowset >> rr) & 1u) {
+                        const uint32_t piece = (cube >> (3 * rr)) & 7u;
+                        if (piece) atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], piece << sh);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+
+        // 3. the next generation of the inner rows, in place: step z reads
+        // row z and writes row z - 1, whose sums are already in registers
+        {
+            const uint32_t w0 = lane < kB3Pitch ? box[lane] : 0u;
+            const uint32_t w1 = lane < kB3Pitch ? box[lane + kB3Pitch] : 0u;
+            B3Q qa = b3_sxy(w0), qb = b3_sxy(w1);
+            uint32_t alive = w1;
+            for (int z = 2; z < kB3Pitch; ++z) {
+                const uint32_t w = lane < kB3Pitch ? box[lane + kB3Pitch * z] : 0u;
+                const B3Q qc = b3_sxy(w);
+                const B3T tt = b3_add3(qa, qb, qc);
+                uint32_t nw;
+                if constexpr (B5S45)
+                    nw = b3_eq<5>(tt) | (alive & b3_eq<6>(tt));
+                else
+                    nw = b3_rule(tt, alive, both, sonly, bonly);
+                if (lane >= 1 && lane <= 27) box[lane + kB3Pitch * (z - 1)] = nw & 0x0ffffffeu;
+                qa = qb;
+                qb = qc;
+                alive = w;
+            }
+        }
+        __syncwarp();
+
+        // 4. the results, 32 blocks at a time
+        for (int j0 = 0; j0 < nblk; j0 += 32) {
+            const int nhere = min(32, nblk - j0);
+            if (lane < nhere) {
+                const uint32_t bp = BP[j0 + lane];
+                const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
+                uint32_t m = 0u;
+#pragma unroll
+                for (int rr = 0; rr < 9; ++rr) {
+                    if ((rowset >> rr) & 1u)
+                        m |= RT[rr * 8 + ((box[rb + rr % 3 + kB3Pitch * (rr / 3)] >> sh) & 7u)];
+                }
+                uint32_t *wp = reinterpret_cast<uint32_t *>(io + k * lane);
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    if (q < kw) wp[q] = (((m >> (4 * q)) & 0xfu) * 0x00204081u) & 0x01010101u;  // bit i -> byte i
+            }
+            __syncwarp();
+            b3_copy_out(tout + (int64_t)k * j0, io, k * nhere, lane);
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace fr

@@ -12,6 +12,21 @@
 
 namespace fr {
 
+// Tables of the bit3 policy (bit3.cuh: 3D, s = 3, tiles of three levels),
+// as word offsets into the plan's `pos` array.  The first `nshared` words
+// (cube bits per word nibble, result bits per row piece, block positions)
+// are copied to shared memory; the halo tables stay in global memory.
+struct Bit3Args {
+    int k = 0;             // cells per level-1 block (a multiple of 4)
+    uint32_t rowset = 0;   // rows dy + 3 dz of a block's 3x3x3 cube that hold members
+    int off_rt = 0;        // result bits of row piece (row, 3 bits): 9 x 8 words
+    int off_bp = 0;        // block j -> box row of its first row | bit shift << 16: k^2 words
+    int nshared = 0;       // words copied to shared memory
+    int off_x = 0;         // inner rows: compact offsets of their x-halo cells, 729 words
+    int off_full = 0;      // rows with y or z on the halo: 112 x 32 cell entries
+    int off_warp = 0;      // byte offset of warp 0's box in shared memory
+};
+
 // Tiled compact step (Sec. 3 stencil procedure, done per subtree).
 // A tile is the k^L cells whose digits above level L agree: one level-L
 // subtree, contiguous in omega, whose cells fill an s^L-wide box in the
@@ -55,6 +70,7 @@ struct StepPlan {
     int nq = 0;                  // tap mode: units per tile
     uint32_t row_sel[8] = {};    // quad mode: byte selectors, group cells -> block rows
     uint32_t pack_sel[9] = {};   // quad mode: byte selectors, block sums -> cell order
+    Bit3Args b3;                 // bit3 mode
 };
 
 // Bounding-box step (Sec. 4 "BB"): membership of a box cell is decided from

@@ -54,6 +54,7 @@
 #include "tma.cuh"
 #include "rows_layout.h"
 #include "lid_layout.h"
+#include "bit3_layout.h"
 
 namespace fr {
 
@@ -90,6 +91,7 @@ struct StepArgs {
     int16_t rel_of_lid[kMaxGroup];  // cell of the group -> box offset from the window base
     uint32_t row_sel[8];            // quad: cells -> block row j (two selectors per row)
     uint32_t pack_sel[9];           // quad: block sums -> cell order (three per word)
+    Bit3Args b3;                    // bit3 policy: its tables in `tab`
 };
 
 // --------------------------------------------------------------- host plan
@@ -148,6 +150,88 @@ static int64_t host_nu(const fractal *f, const int q[3], int L)
 }
 
 static int nbr_width(int dim) { return dim == 3 ? 28 : 8; }  // 26 or 8 entries, 16-byte rows
+
+// ---- bit3 mode (3D fractals with s = 3, see bit3.cuh): tiles of three
+// levels, level-1 blocks of k bytes read as k / 4 words
+static bool bit3_ok(const fractal *f, int L)
+{
+    return f->dim == 3 && f->s == 3 && !f->mixed && L == 3 && f->r >= 3 && f->k % 4 == 0 && f->k <= 24;
+}
+
+static int bit3_shared_words(const fractal *f) { return (f->k / 4) * 16 + 72 + f->k * f->k; }
+
+// The bit3 tables, in the order of Bit3Args: cube bits of each nibble of
+// each word of a block; result bits of each 3-bit row piece; box row and bit
+// shift of each block of a tile; the compact offsets of the x-halo cells of
+// the 729 inner rows; the cells of the 112 rows with y or z on the halo.
+static std::vector<uint32_t> bit3_tables(const fractal *f, Bit3Args &b)
+{
+    const int k = f->k, kw = k / 4;
+    std::vector<uint32_t> t;
+    b.k = k;
+    for (int q = 0; q < kw; ++q)
+        for (int nib = 0; nib < 16; ++nib) {
+            uint32_t m = 0;
+            for (int i = 0; i < 4; ++i)
+                if ((nib >> i) & 1) {
+                    const int32_t *o = &f->offsets[(size_t)(4 * q + i) * 3];
+                    m |= 1u << (o[0] + 3 * o[1] + 9 * o[2]);
+                }
+            t.push_back(m);
+        }
+    b.off_rt = (int)t.size();
+    b.rowset = 0;
+    for (int rr = 0; rr < 9; ++rr)             // row rr = dy + 3 dz of the cube
+        for (int piece = 0; piece < 8; ++piece) {
+            uint32_t m = 0;
+            for (int x = 0; x < 3; ++x) {
+                const int h = f->dev.hinv[x + 3 * rr];
+                if (h < 0) continue;
+                b.rowset |= 1u << rr;
+                if ((piece >> x) & 1) m |= 1u << h;
+            }
+            t.push_back(m);
+        }
+    b.off_bp = (int)t.size();
+    for (int j = 0; j < k * k; ++j) {
+        int c[3];
+        host_lambda(f, j, 2, c);   // block j of a tile: its place in the 9^3 grid of blocks
+        const int rb = (1 + 3 * c[1]) + kB3Pitch * (1 + 3 * c[2]);
+        t.push_back((uint32_t)rb | (uint32_t)(1 + 3 * c[0]) << 16);
+    }
+    b.nshared = (int)t.size();
+    while (t.size() % 4) t.push_back(0);
+    b.off_x = (int)t.size();
+    for (int i = 0; i < kB3Inner; ++i) {
+        const int y = i % 27, z = i / 27;
+        const int ql[3] = {26, y, z}, qr[3] = {0, y, z};
+        const int64_t lo = host_nu(f, ql, 3), hi = host_nu(f, qr, 3);
+        t.push_back((uint32_t)(lo < 0 ? 0xffff : lo) | (uint32_t)(hi < 0 ? 0xffff : hi) << 16);
+    }
+    while (t.size() % 32) t.push_back(0);
+    b.off_full = (int)t.size();
+    for (int i = 0; i < kB3FullRows; ++i) {
+        const int row = b3_full_row(i), y = row % kB3Pitch, z = row / kB3Pitch;
+        for (int lane = 0; lane < 32; ++lane) {
+            uint32_t e = 0xffffffffu;
+            if (lane < kB3Pitch) {
+                const int c[3] = {lane - 1, y - 1, z - 1};
+                int q = 0, m3 = 1, w[3];
+                for (int a = 0; a < 3; ++a) {
+                    const int d = c[a] < 0 ? -1 : (c[a] >= 27 ? 1 : 0);
+                    w[a] = c[a] - 27 * d;
+                    q += (d + 1) * m3;
+                    m3 *= 3;
+                }
+                const int slot = q < 13 ? q : q - 1;
+                const int64_t lw = host_nu(f, w, 3);
+                if (lw >= 0) e = (uint32_t)lw | (uint32_t)slot << 16;
+            }
+            t.push_back(e);
+        }
+    }
+    return t;
+}
 static int nstages() { return 3; }
 
 // Group mode applies to 2D fractals whose block side s^G is 3 or 4.
@@ -160,7 +244,7 @@ static int group_levels(const fractal *f)
 }
 
 enum { kModeCell = 0, kModeGroup3 = 3, kModeGroup4 = 4, kModeQuad = 9, kModeTap = 10, kModeRows0 = 11, kModeRows1 = 12, kModeLid1 = 13,
-       kModeBox3 = 14 };
+       kModeBox3 = 14, kModeBit3 = 15 };
 
 // ---- box3 mode (3D fractals, see box3.cuh): box row pitch, a multiple of
 // 16 bytes with at least one zero word after the B + 2 padded cells
@@ -698,6 +782,14 @@ static Geometry plan_geometry(const fractal *f, int L)
             return g;
         }
     }
+    if (bit3_ok(f, L)) {
+        g.mode = kModeBit3;
+        g.G = 0;
+        g.Px = g.Py = g.planes = 0;
+        g.tab_entries = 0;
+        g.box_bytes = 0;
+        return g;
+    }
     if (f->dim == 3) {
         const int64_t Px = box3_pitch(g.B), vol = Px * (g.B + 2) * (g.B + 2);
         if (Px <= 64 && vol < 65536) {
@@ -752,6 +844,13 @@ static Layout plan_layout(const fractal *f, int L)
     Layout y;
     Geometry g = plan_geometry(f, L);
     int64_t KL = cells_below(f, L);
+    if (g.mode == kModeBit3) {
+        // no stages: the shared tables, then each warp's box and buffer
+        y = Layout();
+        y.off_box = round16(4 * bit3_shared_words(f));
+        y.total = y.off_box + (int64_t)kB3Warps * kB3WarpBytes;
+        return y;
+    }
     y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1 ||
                 g.mode == kModeLid1 || g.mode == kModeBox3) ? 2 : nstages();
     if (f->stages_user >= 2) y.nstage = f->stages_user;
@@ -854,6 +953,32 @@ static int configure(StepPlan &p, int num_sms)
     return FR_OK;
 }
 
+template <bool MULTI, bool B5S45>
+__global__ void step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out);
+
+// bit3 mode: eight tiles (warps) per block
+static int configure_bit3(StepPlan &p, int num_sms)
+{
+    int per_sm = 0, dev = 0, optin = 0;
+    FR_CUDA(cudaGetDevice(&dev));
+    FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (p.smem > optin) {
+        set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
+        return FR_EINVAL;
+    }
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_bit3_kernel<false, false>, p.block, p.smem));
+    if (per_sm < 1) {
+        set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
+        return FR_EINVAL;
+    }
+    p.per_sm = per_sm;
+    p.grid = (int)std::min<int64_t>((int64_t)per_sm * num_sms, (p.NT + kB3Warps - 1) / kB3Warps);
+    return FR_OK;
+}
+
 // Selector nibble that yields a zero byte (sign of a byte whose msb is 0).
 static constexpr uint32_t kZeroSel = 0x8;
 
@@ -908,7 +1033,11 @@ int ensure_step_plan(fractal *f)
     }
 
     std::vector<uint32_t> tab, ring;
-    if (p.mode == kModeTap) {
+    if (p.mode == kModeBit3) {
+        tab = bit3_tables(f, p.b3);
+        p.b3.off_warp = (int)y.off_box;
+        p.nstage = 0;
+    } else if (p.mode == kModeTap) {
         const TapTables t = tap_tables(f, L);
         p.KG = 9;
         p.tapz = t.zero_off;
@@ -1063,7 +1192,8 @@ int ensure_step_plan(fractal *f)
         FR_CUDA(cudaGetLastError());
         FR_CUDA(cudaDeviceSynchronize());
     }
-    if (dim == 3) rc = p.mode == kModeBox3 ? configure<3, kModeBox3>(p, f->num_sms) : configure<3, kModeCell>(p, f->num_sms);
+    if (p.mode == kModeBit3) rc = configure_bit3(p, f->num_sms);
+    else if (dim == 3) rc = p.mode == kModeBox3 ? configure<3, kModeBox3>(p, f->num_sms) : configure<3, kModeCell>(p, f->num_sms);
     else if (p.mode == kModeQuad) rc = configure<2, kModeQuad>(p, f->num_sms);
     else if (p.mode == kModeTap) rc = configure<2, kModeTap>(p, f->num_sms);
     else if (p.mode == kModeRows0) rc = configure<2, kModeRows0>(p, f->num_sms);
@@ -1673,6 +1803,10 @@ __device__ __forceinline__ void tile_rule(const StepArgs &a, int64_t Tg, Rule &r
     if (!MULTI) r = a.rule;
     else r = a.insts[__ldg(a.tile_inst + Tg)].rule;
 }
+
+}  // namespace fr
+#include "bit3.cuh"
+namespace fr {
 
 // Issue the bulk loads of a tile into one stage: its table row and the
 // 16-byte-aligned part of its bytes that lies inside the instance's buffer.
@@ -2314,6 +2448,7 @@ static void fill_args(const fractal *f, StepArgs &a)
     }
     for (int q = 0; q < 8; ++q) a.row_sel[q] = p.row_sel[q];
     for (int q = 0; q < 9; ++q) a.pack_sel[q] = p.pack_sel[q];
+    a.b3 = p.b3;
 }
 
 template <bool MULTI>
@@ -2321,6 +2456,16 @@ static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t
                     cudaStream_t st)
 {
     const StepPlan &p = f->plan;
+    if (p.mode == kModeBit3) {
+        // a warp per tile; the B5/S45 rule with constants where the launch has one rule
+        grid = (int)std::min<int64_t>(grid, (a.NT + kB3Warps - 1) / kB3Warps);
+        if (!MULTI && a.rule.birth == (1u << 5) && a.rule.survive == ((1u << 4) | (1u << 5)))
+            step_bit3_kernel<MULTI, !MULTI><<<grid, p.block, p.smem, st>>>(a, in, out);
+        else
+            step_bit3_kernel<MULTI, false><<<grid, p.block, p.smem, st>>>(a, in, out);
+        FR_CUDA(cudaGetLastError());
+        return FR_OK;
+    }
     if (f->dim == 3 && p.mode == kModeBox3)
         step_tma_kernel<3, kModeBox3, MULTI><<<grid, p.block, p.smem, st>>>(f->dev, a, in, out);
     else if (f->dim == 3)
@@ -2662,6 +2807,7 @@ int autotune_step(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth, u
             f->stages_user = ns;
             if (plan_layout(f, L).total > 200 * 1024) continue;
             if (ensure_step_plan(f) != FR_OK) continue;
+            if (f->plan.mode == kModeBit3 && ns > 2) continue;   // it has no input stages
             int rc = FR_OK;
             for (int w = 0; w < 2 && !rc; ++w) rc = launch_step_once(f, in, out, birth, survive, st);
             if (!rc) rc = (cudaEventRecord(e0, st) == cudaSuccess) ? FR_OK : FR_ECUDA;

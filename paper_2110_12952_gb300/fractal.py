@@ -250,7 +250,7 @@ class Fractal:
     def pipeline_stages(self, stages: int):
         self._check(self._lib.fractal_set_pipeline_stages(self._h, int(stages)))
 
-    POLICIES = {0: "cell", 3: "group3", 4: "group4", 9: "quad", 10: "tap", 11: "rows_carpet", 12: "rows_vicsek", 13: "lid_vicsek", 14: "box3"}
+    POLICIES = {0: "cell", 3: "group3", 4: "group4", 9: "quad", 10: "tap", 11: "rows_carpet", 12: "rows_vicsek", 13: "lid_vicsek", 14: "box3", 15: "bit3"}
 
     def plan_info(self) -> dict:
         """The step's launch plan (``fractal_plan_info``)."""

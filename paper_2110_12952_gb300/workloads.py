@@ -128,6 +128,8 @@ TRI_R20 = Instance(TRIANGLE, 20, 0.3, 3, 1000)
 CARPET_R10 = Instance(CARPET, 10, 0.5, 4, 500)
 VICSEK_R12 = Instance(VICSEK, 12, 0.5, 5, 500)
 MENGER_R6 = Instance(MENGER, 6, 0.5, 6, 500)
+#: One level above the Menger config: 1.28e9 cells, far larger than L2.
+MENGER_R7 = Instance(MENGER, 7, 0.5, 7, 500)
 
 #: Level ranges of the batched / served mixes.
 MIX_LEVELS = {"triangle": (6, 14), "carpet": (3, 8), "vicsek": (3, 9)}

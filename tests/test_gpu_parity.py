@@ -424,10 +424,14 @@ def test_plan_info(P):
     v.tile_levels = 2
     assert v.plan_info()["policy_name"] == "rows_vicsek"
     m = gpu_fr(P, W.MENGER, 4)
+    m.tile_levels = 2
+    mi = m.plan_info()
+    # a 9^3 box in 16-byte rows and its totals box: two stages
+    assert mi["policy_name"] == "box3" and mi["stages"] == 2 and mi["smem_bytes"] <= 100 * 1024
     m.tile_levels = 3
     mi = m.plan_info()
-    # a 27^3 box in 32-byte rows, its totals box and 16-bit offsets: two stages, two CTAs per SM
-    assert mi["policy_name"] == "box3" and mi["stages"] == 2 and mi["smem_bytes"] <= 100 * 1024
+    # a warp per 27^3 tile, its box as 29 x 29 row words: no stages, 8 tiles per block
+    assert mi["policy_name"] == "bit3" and mi["stages"] == 0 and mi["block"] == 256
     arr = (ctypes.c_int32 * 8)()
     assert g._lib.fractal_plan_info(g._h, arr, 0) != 0
     assert g._lib.fractal_plan_info(g._h, arr, 8) != 0
