@@ -9,9 +9,9 @@
 // z-sums slid down z in registers.  Included by step.cu after its helpers.
 //
 // Per tile the warp
-//   1. fetches the halo: the 112 box rows with y or z on the halo, one cell
-//      per lane and a ballot per row, then the two x-halo bits of the other
-//      729 rows, one row per lane;
+//   1. fetches the halo: the level-1 blocks of the existing neighbour tiles
+//      that touch the box's one-cell ring, converted as in 2 and cut to the
+//      ring;
 //   2. turns the tile's cells into box bits.  A level-1 block is k bytes
 //      (consecutive in omega) filling a 3x3x3 cube; four cells of a word
 //      become a nibble through a carry-free multiply, a table maps each
@@ -20,9 +20,11 @@
 //      a row);
 //   3. replaces the inner rows by the next generation, walking down z;
 //   4. reads each block's row pieces back, a table maps them to the block's
-//      k result bits, and a multiply spreads each nibble into four bytes.
-// The tile's bytes move through a per-warp buffer of 32 blocks, so that
-// global loads and stores are whole 16-byte words.
+//      k result bits in the tile's bit string, and a multiply spreads each
+//      nibble of that string into four bytes.
+// The tile's bytes arrive in a per-warp stage by asynchronous 16-byte copies
+// issued while the previous tile is computed; the results are gathered into
+// a bit string in omega order and leave as whole 16-byte words.
 #pragma once
 
 #include <stdint.h>
@@ -117,39 +119,33 @@ __device__ __forceinline__ uint32_t b3_rule(const B3T &t, uint32_t alive, uint32
     return e | (alive & es) | (~alive & eb);
 }
 
-// Copy n bytes (a multiple of 4) between global memory and the warp's
-// buffer: 16-byte words when the global side allows, else 4-byte words or
-// bytes.
-__device__ __forceinline__ void b3_copy_in(uint8_t *dst, const uint8_t *src, int n, int lane)
+// A tile's bytes into the warp's stage: asynchronous 16-byte copies
+// (cp.async, completed by b3_wait) when the source is 16-byte aligned,
+// else plain loads.  n = k^3 is a multiple of 64.
+__device__ __forceinline__ void b3_issue(uint8_t *stage, const uint8_t *src, int n, int lane)
 {
-    if ((((uintptr_t)src) & 15) == 0 && (n & 15) == 0) {
+    if ((((uintptr_t)src) & 15) == 0) {
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(stage);
         for (int i = lane; i < n / 16; i += 32)
-            reinterpret_cast<uint4 *>(dst)[i] = __ldg(reinterpret_cast<const uint4 *>(src) + i);
-    } else if ((((uintptr_t)src) & 3) == 0) {
-        for (int i = lane; i < n / 4; i += 32)
-            reinterpret_cast<uint32_t *>(dst)[i] = __ldg(reinterpret_cast<const uint32_t *>(src) + i);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * i), "l"(src + 16 * i)
+                         : "memory");
     } else {
-        for (int i = lane; i < n; i += 32) dst[i] = __ldg(src + i);
+        for (int i = lane; i < n; i += 32) stage[i] = __ldg(src + i);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void b3_copy_out(uint8_t *dst, const uint8_t *src, int n, int lane)
-{
-    if ((((uintptr_t)dst) & 15) == 0 && (n & 15) == 0) {
-        for (int i = lane; i < n / 16; i += 32)
-            reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
-    } else if ((((uintptr_t)dst) & 3) == 0) {
-        for (int i = lane; i < n / 4; i += 32)
-            reinterpret_cast<uint32_t *>(dst)[i] = reinterpret_cast<const uint32_t *>(src)[i];
-    } else {
-        for (int i = lane; i < n; i += 32) dst[i] = src[i];
-    }
-}
+__device__ __forceinline__ void b3_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// 4 bits -> 4 bytes of 0/1 (bit i lands in bit 8i; the other partial
+// products fall on distinct non-multiples of 8, so nothing carries)
+__device__ __forceinline__ uint32_t b3_nib_bytes(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
 
 // B5S45: the rule is B5/S45 (totals 5 for birth, 5 and 6 for survival),
 // evaluated with constants; otherwise the rule of the tile's instance.
-template <bool MULTI, bool B5S45>
-__global__ void __launch_bounds__(32 * kB3Warps, 4)
+// KW: words per level-1 block (k / 4), or 0 when read from the arguments.
+template <bool MULTI, bool B5S45, int KW>
+__global__ void __launch_bounds__(32 * kB3Warps, 2)
 step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -157,86 +153,97 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
     for (int i = threadIdx.x; i < a.b3.nshared; i += blockDim.x) stab[i] = __ldg(a.tab + i);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *box = reinterpret_cast<uint32_t *>(smem + a.b3.off_warp + warp * kB3WarpBytes);
-    uint8_t *io = reinterpret_cast<uint8_t *>(box + kB3BoxWords);
-    const uint32_t *CT = stab, *RT = stab + a.b3.off_rt, *BP = stab + a.b3.off_bp;
-    const uint32_t *tabx = a.tab + a.b3.off_x, *tabf = a.tab + a.b3.off_full;
-    const int k = a.b3.k, kw = k / 4, nblk = k * k;
-    const int64_t KL = a.KL;
-    const uint32_t rowset = a.b3.rowset;
+    uint8_t *wb = smem + a.b3.off_warp + warp * a.b3.warp_bytes;
+    uint32_t *box = reinterpret_cast<uint32_t *>(wb);
+    const uint8_t **nbase = reinterpret_cast<const uint8_t **>(wb + kB3OffPtr);
+    uint32_t *bits = reinterpret_cast<uint32_t *>(wb + kB3OffBits);
+    uint8_t *stage = wb + a.b3.off_stage;
+    const uint32_t *CT = stab, *RT = stab + a.b3.off_rt, *BP = stab + a.b3.off_bp, *HS = stab + a.b3.off_hs;
+    const uint2 *HE = reinterpret_cast<const uint2 *>(stab + a.b3.off_he);
+    const int k = KW ? 4 * KW : a.b3.k, kw = KW ? KW : k / 4, nblk = k * k;
+    const int64_t KL = a.KL, stride = (int64_t)gridDim.x * kB3Warps;
+    const int nbw = (int)(KL / 32);
 
-    for (int64_t Tg = (int64_t)blockIdx.x * kB3Warps + warp; Tg < a.NT; Tg += (int64_t)gridDim.x * kB3Warps) {
+    int64_t Tg = (int64_t)blockIdx.x * kB3Warps + warp;
+    if (Tg < a.NT) {
+        const TileRef t0 = resolve<MULTI>(a, in, out, Tg);
+        b3_issue(stage, t0.in + t0.T * KL, (int)KL, lane);
+    }
+    for (; Tg < a.NT; Tg += stride) {
         const TileRef t = resolve<MULTI>(a, in, out, Tg);
         Rule rule;
         tile_rule<MULTI>(a, Tg, rule);
         const uint32_t mb = rule.birth & 0x7ffffffu, ms = (rule.survive << 1) & 0xffffffeu;
         const uint32_t both = mb & ms, sonly = ms & ~mb, bonly = mb & ~ms;
-        const int32_t nb = lane < 26 ? __ldg(t.nbr + t.T * a.nbrw + lane) : -1;
-        const uint8_t *src = t.in;
-        const uint8_t *tin = t.in + t.T * KL;
         uint8_t *tout = t.out + t.T * KL;
+        // neighbour tiles by slot
+        const int32_t tn = lane < 26 ? __ldg(t.nbr + t.T * a.nbrw + lane) : -1;
+        const uint32_t present = __ballot_sync(0xffffffffu, tn >= 0);
+        if (lane < 26) nbase[lane] = tn >= 0 ? t.in + (int64_t)tn * KL : t.in;
 
-        // 1. the halo.  Rows with y or z on the halo: lane x holds cell
-        // x - 1 of the row (entry: neighbour slot << 16 | its local omega)
-        for (int i0 = 0; i0 < kB3FullRows; i0 += 8) {
-            uint32_t v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t e = __ldg(tabf + (i0 + j) * 32 + lane);
-                const int32_t tn = __shfl_sync(0xffffffffu, nb, (int)(e >> 16) & 31);
-                v[j] = 0u;
-                if (e != 0xffffffffu && tn >= 0) v[j] = __ldg(src + (int64_t)tn * KL + (e & 0xffffu));
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t w = __ballot_sync(0xffffffffu, v[j] != 0u) & 0x1fffffffu;
-                if (lane == j) box[b3_full_row(i0 + j)] = w;
-            }
-        }
-        // inner rows: cell -1 from the -x tile (slot 12), cell 27 from the
-        // +x tile (slot 13); the tile's own cells are ORed in below
-        {
-            const int32_t tl = __shfl_sync(0xffffffffu, nb, 12), tr = __shfl_sync(0xffffffffu, nb, 13);
-#pragma unroll 4
-            for (int i = lane; i < kB3Inner; i += 32) {
-                const uint32_t e = __ldg(tabx + i);
-                const uint32_t lo = e & 0xffffu, hi = e >> 16;
-                uint32_t w = 0u;
-                if (tl >= 0 && lo != 0xffffu) w = __ldg(src + (int64_t)tl * KL + lo) != 0;
-                if (tr >= 0 && hi != 0xffffu) w |= (uint32_t)(__ldg(src + (int64_t)tr * KL + hi) != 0) << 28;
-                const int z = i / 27;
-                box[(1 + i - 27 * z) + kB3Pitch * (1 + z)] = w;
-            }
-        }
+        // 1. the halo: the blocks of the neighbour tiles that touch the box's
+        // halo ring, converted like the tile's own blocks, their row pieces
+        // cut to the ring (entries grouped by neighbour slot; absent tiles
+        // are skipped)
+        for (int i = lane; i < kB3BoxWords / 4; i += 32) reinterpret_cast<uint4 *>(box)[i] = make_uint4(0, 0, 0, 0);
         __syncwarp();
-
-        // 2. the tile's cells, 32 blocks at a time
-        for (int j0 = 0; j0 < nblk; j0 += 32) {
-            const int nhere = min(32, nblk - j0);
-            b3_copy_in(io, tin + (int64_t)k * j0, k * nhere, lane);
-            __syncwarp();
-            if (lane < nhere) {
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(io + k * lane);
+        const bool al4 = (((uintptr_t)t.in) & 3) == 0;
+        for (uint32_t pm = present & 0x3ffffffu; pm; pm &= pm - 1) {
+            const int d = __ffs(pm) - 1;
+            const uint32_t hs = HS[d];
+            const uint8_t *nt = nbase[d];
+            for (int e = (int)(hs & 0xffffu) + lane; e < (int)(hs >> 16); e += 32) {
+                const uint2 en = HE[e];
+                const uint8_t *src = nt + k * (int)((en.x >> 5) & 1023u);
                 uint32_t cube = 0u;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    if (q < kw) {
-                        const uint32_t w = wp[q];
-                        const uint32_t c = (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;  // bit 7 of a nonzero byte
-                        cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];                            // bits 7,15,23,31 -> 28..31
+                for (int q = 0; q < (KW ? KW : 6); ++q) {
+                    if (KW || q < kw) {
+                        uint32_t w;
+                        if (al4)
+                            w = __ldg(reinterpret_cast<const uint32_t *>(src) + q);
+                        else
+                            w = __ldg(src + 4 * q) | (uint32_t)__ldg(src + 4 * q + 1) << 8 |
+                                (uint32_t)__ldg(src + 4 * q + 2) << 16 | (uint32_t)__ldg(src + 4 * q + 3) << 24;
+                        const uint32_t c = (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;
+                        cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];
                     }
                 }
-                const uint32_t bp = BP[j0 + lane];
-                const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
+                const uint32_t rmask = (en.x >> 15) & 511u, pmask = (en.x >> 24) & 7u, sh2 = en.x >> 27;
+                const int rb = (int)en.y;
 #pragma unroll
-                for (int rr = 0; rr < 9; ++rr) {
-                    if ((rowset >> rr) & 1u) {
-                        const uint32_t piece = (cube >> (3 * rr)) & 7u;
-                        if (piece) atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], piece << sh);
-                    }
+                for (int rr = 0; rr < 9; ++rr)
+                    if ((rmask >> rr) & 1u)
+                        atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], (((cube >> (3 * rr)) & pmask) << sh2) >> 2);
+            }
+        }
+        b3_wait();
+        __syncwarp();
+
+        // 2. the tile's cells, a block per lane, ORed into their rows
+        for (int j = lane; j < nblk; j += 32) {
+            const uint32_t *wp = reinterpret_cast<const uint32_t *>(stage + k * j);
+            uint32_t cube = 0u;
+#pragma unroll
+            for (int q = 0; q < (KW ? KW : 6); ++q) {
+                if (KW || q < kw) {
+                    const uint32_t w = wp[q];
+                    const uint32_t c = (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;  // bit 7 of a nonzero byte
+                    cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];                            // bits 7,15,23,31 -> 28..31
                 }
             }
-            __syncwarp();
+            const uint32_t bp = BP[j];
+            const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
+#pragma unroll
+            for (int rr = 0; rr < 9; ++rr)
+                atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], ((cube >> (3 * rr)) & 7u) << sh);
+        }
+        for (int i = lane; i < nbw; i += 32) bits[i] = 0u;
+        __syncwarp();
+        // the stage is free: the next tile's bytes arrive during the rest
+        if (Tg + stride < a.NT) {
+            const TileRef tn2 = resolve<MULTI>(a, in, out, Tg + stride);
+            b3_issue(stage, tn2.in + tn2.T * KL, (int)KL, lane);
         }
 
         // 3. the next generation of the inner rows, in place: step z reads
@@ -246,6 +253,7 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
             const uint32_t w1 = lane < kB3Pitch ? box[lane + kB3Pitch] : 0u;
             B3Q qa = b3_sxy(w0), qb = b3_sxy(w1);
             uint32_t alive = w1;
+#pragma unroll 3
             for (int z = 2; z < kB3Pitch; ++z) {
                 const uint32_t w = lane < kB3Pitch ? box[lane + kB3Pitch * z] : 0u;
                 const B3Q qc = b3_sxy(w);
@@ -263,27 +271,31 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         }
         __syncwarp();
 
-        // 4. the results, 32 blocks at a time
-        for (int j0 = 0; j0 < nblk; j0 += 32) {
-            const int nhere = min(32, nblk - j0);
-            if (lane < nhere) {
-                const uint32_t bp = BP[j0 + lane];
-                const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
-                uint32_t m = 0u;
+        // 4. the results: each block's k bits (a table per row piece) into
+        // the tile's bit string, then 16 cells per lane and step to memory
+        for (int j = lane; j < nblk; j += 32) {
+            const uint32_t bp = BP[j];
+            const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
+            uint32_t m = 0u;
 #pragma unroll
-                for (int rr = 0; rr < 9; ++rr) {
-                    if ((rowset >> rr) & 1u)
-                        m |= RT[rr * 8 + ((box[rb + rr % 3 + kB3Pitch * (rr / 3)] >> sh) & 7u)];
-                }
-                uint32_t *wp = reinterpret_cast<uint32_t *>(io + k * lane);
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    if (q < kw) wp[q] = (((m >> (4 * q)) & 0xfu) * 0x00204081u) & 0x01010101u;  // bit i -> byte i
-            }
-            __syncwarp();
-            b3_copy_out(tout + (int64_t)k * j0, io, k * nhere, lane);
-            __syncwarp();
+            for (int rr = 0; rr < 9; ++rr)
+                m |= RT[rr * 8 + ((box[rb + rr % 3 + kB3Pitch * (rr / 3)] >> sh) & 7u)];
+            const int b = k * j, wi = b >> 5, s = b & 31;
+            atomicOr(&bits[wi], m << s);
+            if (s + k > 32) atomicOr(&bits[wi + 1], m >> (32 - s));
         }
+        __syncwarp();
+        if ((((uintptr_t)tout) & 15) == 0) {
+            for (int h = lane; h < (int)(KL / 16); h += 32) {
+                const uint32_t hw = bits[h >> 1] >> (16 * (h & 1));
+                reinterpret_cast<uint4 *>(tout)[h] =
+                    make_uint4(b3_nib_bytes(hw & 0xfu), b3_nib_bytes((hw >> 4) & 0xfu), b3_nib_bytes((hw >> 8) & 0xfu),
+                               b3_nib_bytes((hw >> 12) & 0xfu));
+            }
+        } else {
+            for (int c = lane; c < (int)KL; c += 32) tout[c] = (uint8_t)((bits[c >> 5] >> (c & 31)) & 1u);
+        }
+        __syncwarp();
     }
 }
 

@@ -13,18 +13,17 @@
 namespace fr {
 
 // Tables of the bit3 policy (bit3.cuh: 3D, s = 3, tiles of three levels),
-// as word offsets into the plan's `pos` array.  The first `nshared` words
-// (cube bits per word nibble, result bits per row piece, block positions)
-// are copied to shared memory; the halo tables stay in global memory.
+// as word offsets into the plan's `pos` array, all copied to shared memory.
 struct Bit3Args {
     int k = 0;             // cells per level-1 block (a multiple of 4)
-    uint32_t rowset = 0;   // rows dy + 3 dz of a block's 3x3x3 cube that hold members
     int off_rt = 0;        // result bits of row piece (row, 3 bits): 9 x 8 words
     int off_bp = 0;        // block j -> box row of its first row | bit shift << 16: k^2 words
+    int off_hs = 0;        // neighbour slot -> its halo entries: first | end << 16, 26 words
+    int off_he = 0;        // halo entries (two words each, grouped by slot)
     int nshared = 0;       // words copied to shared memory
-    int off_x = 0;         // inner rows: compact offsets of their x-halo cells, 729 words
-    int off_full = 0;      // rows with y or z on the halo: 112 x 32 cell entries
-    int off_warp = 0;      // byte offset of warp 0's box in shared memory
+    int off_warp = 0;      // byte offset of warp 0's area in shared memory
+    int off_stage = 0;     // byte offset of the stage in a warp's area
+    int warp_bytes = 0;    // shared memory per warp (box, pointers, result bits, stage)
 };
 
 // Tiled compact step (Sec. 3 stencil procedure, done per subtree).

@@ -158,12 +158,63 @@ static bool bit3_ok(const fractal *f, int L)
     return f->dim == 3 && f->s == 3 && !f->mixed && L == 3 && f->r >= 3 && f->k % 4 == 0 && f->k <= 24;
 }
 
-static int bit3_shared_words(const fractal *f) { return (f->k / 4) * 16 + 72 + f->k * f->k; }
+// halo entries of a 3D fractal with s = 3 at three levels: per neighbour
+// direction, the blocks of that tile which touch the box's one-cell ring
+static std::vector<uint32_t> bit3_halo(const fractal *f, std::vector<uint32_t> &hs)
+{
+    std::vector<uint32_t> he;
+    hs.assign(26, 0u);
+    for (int q = 0; q < 27; ++q) {
+        if (q == 13) continue;
+        const int dir[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+        const int slot = q < 13 ? q : q - 1;
+        const uint32_t first = (uint32_t)(he.size() / 2);
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = dir[a] < 0 ? 8 : 0;   // the neighbour's blocks next to this tile
+            hi[a] = dir[a] > 0 ? 0 : 8;
+        }
+        for (int bz = lo[2]; bz <= hi[2]; ++bz)
+            for (int by = lo[1]; by <= hi[1]; ++by)
+                for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+                    const int c[3] = {bx, by, bz};
+                    const int64_t jb = host_nu(f, c, 2);
+                    if (jb < 0) continue;
+                    // box coordinates of the block's first cell (the box's
+                    // interior is 1 .. 27, its ring 0 and 28)
+                    const int o[3] = {1 + 27 * dir[0] + 3 * bx, 1 + 27 * dir[1] + 3 * by, 1 + 27 * dir[2] + 3 * bz};
+                    uint32_t rmask = 0, pmask = 0;
+                    for (int rr = 0; rr < 9; ++rr) {
+                        const int y = o[1] + rr % 3, z = o[2] + rr / 3;
+                        if (y >= 0 && y <= 28 && z >= 0 && z <= 28) rmask |= 1u << rr;
+                    }
+                    for (int x0 = 0; x0 < 3; ++x0)
+                        if (o[0] + x0 >= 0 && o[0] + x0 <= 28) pmask |= 1u << x0;
+                    const int rowbase = o[1] + kB3Pitch * o[2];
+                    he.push_back((uint32_t)slot | (uint32_t)jb << 5 | rmask << 15 | pmask << 24 |
+                                 (uint32_t)(o[0] + 2) << 27);
+                    he.push_back((uint32_t)rowbase);
+                }
+        hs[slot] = first | (uint32_t)(he.size() / 2) << 16;
+    }
+    return he;
+}
+
+static int bit3_shared_words(const fractal *f)
+{
+    std::vector<uint32_t> hs;
+    const size_t nhe = bit3_halo(f, hs).size();
+    return (int)((f->k / 4) * 16 + 72 + f->k * f->k + 26 + 2 + nhe);
+}
+static int bit3_off_stage(const fractal *f) { return kB3OffBits + (int)round16(((int64_t)f->k * f->k * f->k + 7) / 8); }
+static int bit3_warp_bytes(const fractal *f) { return bit3_off_stage(f) + (int)round16((int64_t)f->k * f->k * f->k); }
 
 // The bit3 tables, in the order of Bit3Args: cube bits of each nibble of
 // each word of a block; result bits of each 3-bit row piece; box row and bit
-// shift of each block of a tile; the compact offsets of the x-halo cells of
-// the 729 inner rows; the cells of the 112 rows with y or z on the halo.
+// shift of each block of a tile; the halo entries by neighbour slot.  A halo
+// entry is slot | block index << 5 | rows in the ring << 15 | cells of a row
+// piece in the ring << 24 | (box bit of the piece's first cell + 2) << 27,
+// then the box row of the block's first row (which may lie outside the box).
 static std::vector<uint32_t> bit3_tables(const fractal *f, Bit3Args &b)
 {
     const int k = f->k, kw = k / 4;
@@ -180,15 +231,12 @@ static std::vector<uint32_t> bit3_tables(const fractal *f, Bit3Args &b)
             t.push_back(m);
         }
     b.off_rt = (int)t.size();
-    b.rowset = 0;
     for (int rr = 0; rr < 9; ++rr)             // row rr = dy + 3 dz of the cube
         for (int piece = 0; piece < 8; ++piece) {
             uint32_t m = 0;
             for (int x = 0; x < 3; ++x) {
                 const int h = f->dev.hinv[x + 3 * rr];
-                if (h < 0) continue;
-                b.rowset |= 1u << rr;
-                if ((piece >> x) & 1) m |= 1u << h;
+                if (h >= 0 && ((piece >> x) & 1)) m |= 1u << h;
             }
             t.push_back(m);
         }
@@ -199,37 +247,14 @@ static std::vector<uint32_t> bit3_tables(const fractal *f, Bit3Args &b)
         const int rb = (1 + 3 * c[1]) + kB3Pitch * (1 + 3 * c[2]);
         t.push_back((uint32_t)rb | (uint32_t)(1 + 3 * c[0]) << 16);
     }
+    std::vector<uint32_t> hs;
+    const std::vector<uint32_t> he = bit3_halo(f, hs);
+    b.off_hs = (int)t.size();
+    t.insert(t.end(), hs.begin(), hs.end());
+    while (t.size() % 2) t.push_back(0);
+    b.off_he = (int)t.size();
+    t.insert(t.end(), he.begin(), he.end());
     b.nshared = (int)t.size();
-    while (t.size() % 4) t.push_back(0);
-    b.off_x = (int)t.size();
-    for (int i = 0; i < kB3Inner; ++i) {
-        const int y = i % 27, z = i / 27;
-        const int ql[3] = {26, y, z}, qr[3] = {0, y, z};
-        const int64_t lo = host_nu(f, ql, 3), hi = host_nu(f, qr, 3);
-        t.push_back((uint32_t)(lo < 0 ? 0xffff : lo) | (uint32_t)(hi < 0 ? 0xffff : hi) << 16);
-    }
-    while (t.size() % 32) t.push_back(0);
-    b.off_full = (int)t.size();
-    for (int i = 0; i < kB3FullRows; ++i) {
-        const int row = b3_full_row(i), y = row % kB3Pitch, z = row / kB3Pitch;
-        for (int lane = 0; lane < 32; ++lane) {
-            uint32_t e = 0xffffffffu;
-            if (lane < kB3Pitch) {
-                const int c[3] = {lane - 1, y - 1, z - 1};
-                int q = 0, m3 = 1, w[3];
-                for (int a = 0; a < 3; ++a) {
-                    const int d = c[a] < 0 ? -1 : (c[a] >= 27 ? 1 : 0);
-                    w[a] = c[a] - 27 * d;
-                    q += (d + 1) * m3;
-                    m3 *= 3;
-                }
-                const int slot = q < 13 ? q : q - 1;
-                const int64_t lw = host_nu(f, w, 3);
-                if (lw >= 0) e = (uint32_t)lw | (uint32_t)slot << 16;
-            }
-            t.push_back(e);
-        }
-    }
     return t;
 }
 static int nstages() { return 3; }
@@ -848,7 +873,7 @@ static Layout plan_layout(const fractal *f, int L)
         // no stages: the shared tables, then each warp's box and buffer
         y = Layout();
         y.off_box = round16(4 * bit3_shared_words(f));
-        y.total = y.off_box + (int64_t)kB3Warps * kB3WarpBytes;
+        y.total = y.off_box + (int64_t)kB3Warps * bit3_warp_bytes(f);
         return y;
     }
     y.nstage = (g.mode == kModeQuad || g.mode == kModeTap || g.mode == kModeRows0 || g.mode == kModeRows1 ||
@@ -883,7 +908,8 @@ static int choose_levels(const fractal *f)
     const int64_t budget = 100 * 1024;
     int best = 0;
     for (int L = 0; L <= f->r; ++L) {
-        if (plan_layout(f, L).total > budget) break;
+        // the bit3 policy's shared memory holds 8 tiles' boxes and stages (two blocks per SM)
+        if (plan_layout(f, L).total > (bit3_ok(f, L) ? 2 * budget : budget)) break;
         best = L;
     }
     while (best < f->r && cells_above(f, best) >= ((int64_t)1 << 31)) ++best;
@@ -953,7 +979,7 @@ static int configure(StepPlan &p, int num_sms)
     return FR_OK;
 }
 
-template <bool MULTI, bool B5S45>
+template <bool MULTI, bool B5S45, int KW>
 __global__ void step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out);
 
 // bit3 mode: eight tiles (warps) per block
@@ -966,10 +992,12 @@ static int configure_bit3(StepPlan &p, int num_sms)
         set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
         return FR_EINVAL;
     }
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_bit3_kernel<false, false>, p.block, p.smem));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<true, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<true, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_bit3_kernel<false, false, 0>, p.block, p.smem));
     if (per_sm < 1) {
         set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
         return FR_EINVAL;
@@ -1036,6 +1064,8 @@ int ensure_step_plan(fractal *f)
     if (p.mode == kModeBit3) {
         tab = bit3_tables(f, p.b3);
         p.b3.off_warp = (int)y.off_box;
+        p.b3.warp_bytes = bit3_warp_bytes(f);
+        p.b3.off_stage = bit3_off_stage(f);
         p.nstage = 0;
     } else if (p.mode == kModeTap) {
         const TapTables t = tap_tables(f, L);
@@ -2458,11 +2488,15 @@ static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t
     const StepPlan &p = f->plan;
     if (p.mode == kModeBit3) {
         // a warp per tile; the B5/S45 rule with constants where the launch has one rule
+        // and the Menger sponge's five words per block with constants
         grid = (int)std::min<int64_t>(grid, (a.NT + kB3Warps - 1) / kB3Warps);
-        if (!MULTI && a.rule.birth == (1u << 5) && a.rule.survive == ((1u << 4) | (1u << 5)))
-            step_bit3_kernel<MULTI, !MULTI><<<grid, p.block, p.smem, st>>>(a, in, out);
+        const bool b5s45 = !MULTI && a.rule.birth == (1u << 5) && a.rule.survive == ((1u << 4) | (1u << 5));
+        if (p.b3.k != 20)
+            step_bit3_kernel<MULTI, false, 0><<<grid, p.block, p.smem, st>>>(a, in, out);
+        else if (b5s45)
+            step_bit3_kernel<MULTI, !MULTI, 5><<<grid, p.block, p.smem, st>>>(a, in, out);
         else
-            step_bit3_kernel<MULTI, false><<<grid, p.block, p.smem, st>>>(a, in, out);
+            step_bit3_kernel<MULTI, false, 5><<<grid, p.block, p.smem, st>>>(a, in, out);
         FR_CUDA(cudaGetLastError());
         return FR_OK;
     }
