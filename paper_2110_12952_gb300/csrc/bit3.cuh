@@ -22,9 +22,10 @@
 //   4. reads each block's row pieces back, a table maps them to the block's
 //      k result bits in the tile's bit string, and a multiply spreads each
 //      nibble of that string into four bytes.
-// The tile's bytes arrive in a per-warp stage by asynchronous 16-byte copies
-// issued while the previous tile is computed; the results are gathered into
-// a bit string in omega order and leave as whole 16-byte words.
+// Each lane reads its blocks' words straight from memory, one block ahead
+// (the first while the halo is fetched); with a small shared-memory area per
+// warp, 32 warps fit on an SM to hide the latency.  The results are gathered
+// into a bit string in omega order and leave as whole 16-byte words.
 #pragma once
 
 #include <stdint.h>
@@ -119,23 +120,39 @@ __device__ __forceinline__ uint32_t b3_rule(const B3T &t, uint32_t alive, uint32
     return e | (alive & es) | (~alive & eb);
 }
 
-// A tile's bytes into the warp's stage: asynchronous 16-byte copies
-// (cp.async, completed by b3_wait) when the source is 16-byte aligned,
-// else plain loads.  n = k^3 is a multiple of 64.
-__device__ __forceinline__ void b3_issue(uint8_t *stage, const uint8_t *src, int n, int lane)
+// The words of the level-1 block at src (k bytes, k = 4 kw): aligned
+// 4-byte loads, or bytes where the buffer is not 4-byte aligned.
+template <int KW>
+__device__ __forceinline__ void b3_load_block(uint32_t (&w)[6], const uint8_t *src, int kw, bool al4)
 {
-    if ((((uintptr_t)src) & 15) == 0) {
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(stage);
-        for (int i = lane; i < n / 16; i += 32)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * i), "l"(src + 16 * i)
-                         : "memory");
-    } else {
-        for (int i = lane; i < n; i += 32) stage[i] = __ldg(src + i);
+#pragma unroll
+    for (int q = 0; q < (KW ? KW : 6); ++q) {
+        if (KW || q < kw) {
+            if (al4)
+                w[q] = __ldg(reinterpret_cast<const uint32_t *>(src) + q);
+            else
+                w[q] = __ldg(src + 4 * q) | (uint32_t)__ldg(src + 4 * q + 1) << 8 |
+                       (uint32_t)__ldg(src + 4 * q + 2) << 16 | (uint32_t)__ldg(src + 4 * q + 3) << 24;
+        }
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void b3_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// The 27-bit cube of a block (bit x + 3y + 9z for its cell at (x, y, z))
+// from its words: bit 7 of each nonzero byte, bits 7, 15, 23, 31 gathered
+// into a nibble by a carry-free multiply, a table per word and nibble.
+template <int KW>
+__device__ __forceinline__ uint32_t b3_cube(const uint32_t (&w)[6], const uint32_t *CT, int kw)
+{
+    uint32_t cube = 0u;
+#pragma unroll
+    for (int q = 0; q < (KW ? KW : 6); ++q) {
+        if (KW || q < kw) {
+            const uint32_t c = (((w[q] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w[q]) & 0x80808080u;
+            cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];
+        }
+    }
+    return cube;
+}
 
 // 4 bits -> 4 bytes of 0/1 (bit i lands in bit 8i; the other partial
 // products fall on distinct non-multiples of 8, so nothing carries)
@@ -145,7 +162,7 @@ __device__ __forceinline__ uint32_t b3_nib_bytes(uint32_t nib) { return (nib * 0
 // evaluated with constants; otherwise the rule of the tile's instance.
 // KW: words per level-1 block (k / 4), or 0 when read from the arguments.
 template <bool MULTI, bool B5S45, int KW>
-__global__ void __launch_bounds__(32 * kB3Warps, 2)
+__global__ void __launch_bounds__(32 * kB3Warps, 4)
 step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -157,25 +174,24 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
     uint32_t *box = reinterpret_cast<uint32_t *>(wb);
     const uint8_t **nbase = reinterpret_cast<const uint8_t **>(wb + kB3OffPtr);
     uint32_t *bits = reinterpret_cast<uint32_t *>(wb + kB3OffBits);
-    uint8_t *stage = wb + a.b3.off_stage;
     const uint32_t *CT = stab, *RT = stab + a.b3.off_rt, *BP = stab + a.b3.off_bp, *HS = stab + a.b3.off_hs;
     const uint2 *HE = reinterpret_cast<const uint2 *>(stab + a.b3.off_he);
     const int k = KW ? 4 * KW : a.b3.k, kw = KW ? KW : k / 4, nblk = k * k;
     const int64_t KL = a.KL, stride = (int64_t)gridDim.x * kB3Warps;
     const int nbw = (int)(KL / 32);
 
-    int64_t Tg = (int64_t)blockIdx.x * kB3Warps + warp;
-    if (Tg < a.NT) {
-        const TileRef t0 = resolve<MULTI>(a, in, out, Tg);
-        b3_issue(stage, t0.in + t0.T * KL, (int)KL, lane);
-    }
-    for (; Tg < a.NT; Tg += stride) {
+    for (int64_t Tg = (int64_t)blockIdx.x * kB3Warps + warp; Tg < a.NT; Tg += stride) {
         const TileRef t = resolve<MULTI>(a, in, out, Tg);
         Rule rule;
         tile_rule<MULTI>(a, Tg, rule);
         const uint32_t mb = rule.birth & 0x7ffffffu, ms = (rule.survive << 1) & 0xffffffeu;
         const uint32_t both = mb & ms, sonly = ms & ~mb, bonly = mb & ~ms;
         uint8_t *tout = t.out + t.T * KL;
+        const uint8_t *tin = t.in + t.T * KL;
+        const bool al4 = (((uintptr_t)t.in) & 3) == 0;
+        // the lane's first block of the tile, loaded while the halo is fetched
+        uint32_t wn[6];
+        if (lane < nblk) b3_load_block<KW>(wn, tin + k * lane, kw, al4);
         // neighbour tiles by slot
         const int32_t tn = lane < 26 ? __ldg(t.nbr + t.T * a.nbrw + lane) : -1;
         const uint32_t present = __ballot_sync(0xffffffffu, tn >= 0);
@@ -187,28 +203,15 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         // are skipped)
         for (int i = lane; i < kB3BoxWords / 4; i += 32) reinterpret_cast<uint4 *>(box)[i] = make_uint4(0, 0, 0, 0);
         __syncwarp();
-        const bool al4 = (((uintptr_t)t.in) & 3) == 0;
         for (uint32_t pm = present & 0x3ffffffu; pm; pm &= pm - 1) {
             const int d = __ffs(pm) - 1;
             const uint32_t hs = HS[d];
             const uint8_t *nt = nbase[d];
             for (int e = (int)(hs & 0xffffu) + lane; e < (int)(hs >> 16); e += 32) {
                 const uint2 en = HE[e];
-                const uint8_t *src = nt + k * (int)((en.x >> 5) & 1023u);
-                uint32_t cube = 0u;
-#pragma unroll
-                for (int q = 0; q < (KW ? KW : 6); ++q) {
-                    if (KW || q < kw) {
-                        uint32_t w;
-                        if (al4)
-                            w = __ldg(reinterpret_cast<const uint32_t *>(src) + q);
-                        else
-                            w = __ldg(src + 4 * q) | (uint32_t)__ldg(src + 4 * q + 1) << 8 |
-                                (uint32_t)__ldg(src + 4 * q + 2) << 16 | (uint32_t)__ldg(src + 4 * q + 3) << 24;
-                        const uint32_t c = (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;
-                        cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];
-                    }
-                }
+                uint32_t w[6];
+                b3_load_block<KW>(w, nt + k * (int)((en.x >> 5) & 1023u), kw, al4);
+                const uint32_t cube = b3_cube<KW>(w, CT, kw);
                 const uint32_t rmask = (en.x >> 15) & 511u, pmask = (en.x >> 24) & 7u, sh2 = en.x >> 27;
                 const int rb = (int)en.y;
 #pragma unroll
@@ -217,21 +220,14 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
                         atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], (((cube >> (3 * rr)) & pmask) << sh2) >> 2);
             }
         }
-        b3_wait();
-        __syncwarp();
-
-        // 2. the tile's cells, a block per lane, ORed into their rows
+        // 2. the tile's cells, a block per lane (the next one loaded ahead),
+        // ORed into their rows
         for (int j = lane; j < nblk; j += 32) {
-            const uint32_t *wp = reinterpret_cast<const uint32_t *>(stage + k * j);
-            uint32_t cube = 0u;
+            uint32_t wc[6];
 #pragma unroll
-            for (int q = 0; q < (KW ? KW : 6); ++q) {
-                if (KW || q < kw) {
-                    const uint32_t w = wp[q];
-                    const uint32_t c = (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;  // bit 7 of a nonzero byte
-                    cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];                            // bits 7,15,23,31 -> 28..31
-                }
-            }
+            for (int q = 0; q < 6; ++q) wc[q] = wn[q];
+            if (j + 32 < nblk) b3_load_block<KW>(wn, tin + k * (j + 32), kw, al4);
+            const uint32_t cube = b3_cube<KW>(wc, CT, kw);
             const uint32_t bp = BP[j];
             const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
 #pragma unroll
@@ -240,11 +236,6 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         }
         for (int i = lane; i < nbw; i += 32) bits[i] = 0u;
         __syncwarp();
-        // the stage is free: the next tile's bytes arrive during the rest
-        if (Tg + stride < a.NT) {
-            const TileRef tn2 = resolve<MULTI>(a, in, out, Tg + stride);
-            b3_issue(stage, tn2.in + tn2.T * KL, (int)KL, lane);
-        }
 
         // 3. the next generation of the inner rows, in place: step z reads
         // row z and writes row z - 1, whose sums are already in registers

@@ -22,8 +22,7 @@ struct Bit3Args {
     int off_he = 0;        // halo entries (two words each, grouped by slot)
     int nshared = 0;       // words copied to shared memory
     int off_warp = 0;      // byte offset of warp 0's area in shared memory
-    int off_stage = 0;     // byte offset of the stage in a warp's area
-    int warp_bytes = 0;    // shared memory per warp (box, pointers, result bits, stage)
+    int warp_bytes = 0;    // shared memory per warp (box, pointers, result bits)
 };
 
 // Tiled compact step (Sec. 3 stencil procedure, done per subtree).

@@ -206,8 +206,7 @@ static int bit3_shared_words(const fractal *f)
     const size_t nhe = bit3_halo(f, hs).size();
     return (int)((f->k / 4) * 16 + 72 + f->k * f->k + 26 + 2 + nhe);
 }
-static int bit3_off_stage(const fractal *f) { return kB3OffBits + (int)round16(((int64_t)f->k * f->k * f->k + 7) / 8); }
-static int bit3_warp_bytes(const fractal *f) { return bit3_off_stage(f) + (int)round16((int64_t)f->k * f->k * f->k); }
+static int bit3_warp_bytes(const fractal *f) { return kB3OffBits + (int)round16(((int64_t)f->k * f->k * f->k + 7) / 8); }
 
 // The bit3 tables, in the order of Bit3Args: cube bits of each nibble of
 // each word of a block; result bits of each 3-bit row piece; box row and bit
@@ -908,8 +907,7 @@ static int choose_levels(const fractal *f)
     const int64_t budget = 100 * 1024;
     int best = 0;
     for (int L = 0; L <= f->r; ++L) {
-        // the bit3 policy's shared memory holds 8 tiles' boxes and stages (two blocks per SM)
-        if (plan_layout(f, L).total > (bit3_ok(f, L) ? 2 * budget : budget)) break;
+        if (plan_layout(f, L).total > budget) break;
         best = L;
     }
     while (best < f->r && cells_above(f, best) >= ((int64_t)1 << 31)) ++best;
@@ -1065,7 +1063,6 @@ int ensure_step_plan(fractal *f)
         tab = bit3_tables(f, p.b3);
         p.b3.off_warp = (int)y.off_box;
         p.b3.warp_bytes = bit3_warp_bytes(f);
-        p.b3.off_stage = bit3_off_stage(f);
         p.nstage = 0;
     } else if (p.mode == kModeTap) {
         const TapTables t = tap_tables(f, L);
