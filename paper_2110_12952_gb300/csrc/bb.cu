@@ -45,7 +45,7 @@ static bool host_member(const fractal *f, int64_t x, int64_t y, int64_t z, int l
 static int build_bitmap(const fractal *f, int side, int levels, int base, uint32_t **out, int64_t *words)
 {
     int64_t n = ipow64(side, f->dim);
-    int64_t nw = (n + 31) / 32;
+    int64_t nw = (n + 31) / 32 + 1;   // one spare word: 32-bit windows may start in the last word
     std::vector<uint32_t> bits(nw, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t x = i % side, y = (i / side) % side, z = f->dim == 3 ? i / ((int64_t)side * side) : 0;
@@ -297,6 +297,224 @@ bb_fast_kernel(BBFastArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
     }
 }
 
+// ---------------------------------------------------------------------
+// Vectorised path for other 2D boxes whose local side S = s^Lb is at least
+// 16 (s = 3 from r = 5 on): the rows need not start 16-byte aligned.  Lane
+// l of a warp holds the 16 cells x0 = 480 sx + 16 l .. x0 + 15 of a row and
+// walks down a strip of rows as bb_fast_kernel does.  The cells' bytes sit
+// at flat offset f = y n + x0, and k = f mod 16 is the same in every lane
+// of the warp: each lane loads the aligned chunk at f - k, takes the next
+// one from the next lane, and shifts.  Membership of the 16 cells is a
+// 16-bit field of the local bitmap's row (split in two where the cells
+// cross into the next local tile, each part gated by its coarse bit); cells
+// past the row's end get no membership.
+//
+// Results go back as whole aligned 16-byte chunks: lane l (0..30) writes the
+// chunk after f - k, its own cells 16 - k .. 15 followed by lane l + 1's
+// cells 0 .. 15 - k (for k = 0: lanes 1..30 their own 16 cells).  Strips
+// advance by 480 cells, so lanes 0 and 31 overlap the neighbouring strips:
+// the cells they write never need the cell beyond them (lane 0 writes cells
+// from 16 - k >= 1 on, lane 31 up to 15 - k <= 14), which is why no lane
+// fetches cells outside its warp; the one chunk per strip boundary is
+// written by both warps with the same bytes.  The head of a row (strip 0,
+// lane 0, before its first chunk) and chunks reaching past the row's end
+// are written byte by byte.
+
+struct BBRowsArgs {
+    int32_t n;            // box side
+    int64_t total;        // n^2 bytes
+    int32_t S, C;         // local / coarse sides (S >= 16)
+    DivU32 sdiv;          // division by S
+    const uint32_t *local_bits, *coarse_bits;
+    int rows;             // rows per warp strip
+    int strips_x;         // strips per row (480 cells apart)
+    int64_t warps;        // strips_x * ceil(n / rows)
+    Rule rule;
+};
+
+// 32 bits of a bitmap from bit pos on (bitmaps carry one spare word)
+__device__ __forceinline__ uint32_t bits32_at(const uint32_t *__restrict__ bits, uint32_t pos)
+{
+    return __funnelshift_r(__ldg(bits + (pos >> 5)), __ldg(bits + (pos >> 5) + 1), pos & 31);
+}
+
+__device__ __forceinline__ uint32_t coarse_bit(const BBRowsArgs &a, int32_t cx, int32_t cy)
+{
+    if (cx >= a.C) return 0u;
+    const uint32_t c = (uint32_t)cy * (uint32_t)a.C + (uint32_t)cx;
+    return (__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u;
+}
+
+// bytes k .. k + 15 of the 32 bytes w[0..7] (k the same in the whole warp)
+__device__ __forceinline__ void bytes16_at(const uint32_t w[8], int k, uint32_t d[4])
+{
+    const uint32_t sh = 8u * (uint32_t)(k & 3);
+    switch (k >> 2) {
+        case 0:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i], w[i + 1], sh);
+            break;
+        case 1:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i + 1], w[i + 2], sh);
+            break;
+        case 2:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i + 2], w[i + 3], sh);
+            break;
+        default:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i + 3], w[i + 4], sh);
+            break;
+    }
+}
+
+// the 16 bytes at in + a (a 16-byte aligned), 0 outside [0, total)
+__device__ __forceinline__ uint4 load16_bounded(const uint8_t *__restrict__ in, int64_t total, int64_t a)
+{
+    if (a >= 0 && a + 16 <= total) return __ldg(reinterpret_cast<const uint4 *>(in + a));
+    uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const uint32_t b = (a + j >= 0 && a + j < total) ? (uint32_t)__ldg(in + a + j) << (8 * (j & 3)) : 0u;
+        if (j < 4) w0 |= b;
+        else if (j < 8) w1 |= b;
+        else if (j < 12) w2 |= b;
+        else w3 |= b;
+    }
+    return make_uint4(w0, w1, w2, w3);
+}
+
+struct RowsRow {
+    uint32_t d[4], m[4], h[4];
+};
+
+// The lane's column constants and the row it stands at: local and coarse
+// row, and the coarse bits of its two possible coarse columns in that
+// coarse row (refreshed when the coarse row changes).
+struct RowsCursor {
+    int32_t x0, xl0, cx0;
+    uint32_t mask1;       // cells of the first local tile
+    int first;            // S - xl0
+    int32_t yl, cy;       // of the next row to process
+    uint32_t c1, c2;      // coarse bits of columns cx0, cx0 + 1 in coarse row cy
+};
+
+__device__ __forceinline__ void rows_cursor_row(const BBRowsArgs &a, RowsCursor &u, int32_t y)
+{
+    const uint32_t cy = divu(a.sdiv, (uint32_t)y);
+    u.yl = y - (int32_t)(cy * (uint32_t)a.S);
+    u.cy = (int32_t)cy;
+    u.c1 = coarse_bit(a, u.cx0, u.cy);
+    u.c2 = u.first < 16 ? coarse_bit(a, u.cx0 + 1, u.cy) : 0u;   // the second local tile only if the cells reach it
+}
+
+// masked 0/1 bytes, member bytes and horizontal 3-sums of the lane's cells
+// in row y (zeros for rows outside the box); lane 0's left and lane 31's
+// right neighbour count as 0 (see above).  Rows come in increasing order,
+// the cursor standing at row y (for rows inside the box).
+__device__ __forceinline__ void rows_process(const BBRowsArgs &a, const uint8_t *__restrict__ in, RowsCursor &u,
+                                             int32_t y, int lane, RowsRow &o)
+{
+    const int32_t x0 = u.x0;
+    uint32_t raw[4] = {0u, 0u, 0u, 0u}, m16 = 0u;
+    if (y >= 0 && y < a.n) {   // the same in the whole warp
+        const int64_t f = (int64_t)y * a.n + x0;
+        const int k = (int)(f & 15);
+        const int64_t a0 = f - k;
+        const uint4 c = load16_bounded(in, a.total, a0);
+        uint4 nx;
+        nx.x = __shfl_down_sync(0xffffffffu, c.x, 1);
+        nx.y = __shfl_down_sync(0xffffffffu, c.y, 1);
+        nx.z = __shfl_down_sync(0xffffffffu, c.z, 1);
+        nx.w = __shfl_down_sync(0xffffffffu, c.w, 1);
+        if (lane == 31) nx = load16_bounded(in, a.total, a0 + 16);
+        const uint32_t w[8] = {c.x, c.y, c.z, c.w, nx.x, nx.y, nx.z, nx.w};
+        bytes16_at(w, k, raw);
+        const uint32_t rowbit = (uint32_t)u.yl * (uint32_t)a.S;
+        m16 = (u.c1 ? bits32_at(a.local_bits, rowbit + (uint32_t)u.xl0) & u.mask1 : 0u) |
+              (u.c2 ? (bits32_at(a.local_bits, rowbit) << (u.first & 31)) & 0xffffu : 0u);
+        if (++u.yl == a.S && y + 1 < a.n) rows_cursor_row(a, u, y + 1);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        o.m[q] = nib_bytes((m16 >> (4 * q)) & 0xfu);
+        o.d[q] = nz_bytes(raw[q]) & o.m[q];
+    }
+    uint32_t left = __shfl_up_sync(0xffffffffu, o.d[3], 1);    // byte 3 = cell x0 - 1
+    uint32_t right = __shfl_down_sync(0xffffffffu, o.d[0], 1); // byte 0 = cell x0 + 16
+    if (lane == 0) left = 0u;
+    if (lane == 31) right = 0u;
+    const uint32_t w[6] = {left, o.d[0], o.d[1], o.d[2], o.d[3], right};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        o.h[q] = w[q + 1] + __funnelshift_l(w[q], w[q + 1], 8) + __funnelshift_r(w[q + 1], w[q + 2], 8);
+}
+
+// The results of row y: lane l's chunk (see above), from its 16 result
+// bytes o; `row_end` is the flat offset of the row's end.
+__device__ __forceinline__ void rows_store(uint8_t *__restrict__ out, int64_t f, int64_t row_end, int32_t x0, int lane,
+                                           const uint32_t o[4])
+{
+    const int k = (int)(f & 15);
+    const uint32_t nx[4] = {__shfl_down_sync(0xffffffffu, o[0], 1), __shfl_down_sync(0xffffffffu, o[1], 1),
+                            __shfl_down_sync(0xffffffffu, o[2], 1), __shfl_down_sync(0xffffffffu, o[3], 1)};
+    const bool head = x0 == 0 && k != 0;   // strip 0, lane 0: the row's first bytes
+    const bool writer = k == 0 ? (lane >= 1 && lane <= 30) || x0 == 0 : lane <= 30;
+    uint32_t c[4];
+    int64_t p;
+    if (k == 0) {
+        c[0] = o[0]; c[1] = o[1]; c[2] = o[2]; c[3] = o[3];
+        p = f;
+    } else {
+        const uint32_t w[8] = {o[0], o[1], o[2], o[3], nx[0], nx[1], nx[2], nx[3]};
+        bytes16_at(w, 16 - k, c);
+        p = f - k + 16;
+    }
+    if (writer && p < row_end) {
+        if (p + 16 <= row_end) {
+            *reinterpret_cast<uint4 *>(out + p) = make_uint4(c[0], c[1], c[2], c[3]);
+        } else {
+            for (int j = 0; j < (int)(row_end - p); ++j) out[p + j] = (uint8_t)(c[j >> 2] >> (8 * (j & 3)));
+        }
+    }
+    if (head) {
+        const int nh = (int)min((int64_t)(16 - k), row_end - f);
+        for (int j = 0; j < nh; ++j) out[f + j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+    }
+}
+
+__global__ void __launch_bounds__(128)
+bb_rows_kernel(BBRowsArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wid >= a.warps) return;   // whole warps leave together
+    const int32_t y0 = (int32_t)(wid / a.strips_x) * a.rows;
+    const int32_t y1 = min(y0 + a.rows, a.n);
+    RowsCursor u;
+    u.x0 = (int32_t)(wid % a.strips_x) * 480 + lane * 16;
+    const uint32_t cx0 = divu(a.sdiv, (uint32_t)u.x0);
+    u.cx0 = (int32_t)cx0;
+    u.xl0 = u.x0 - (int32_t)(cx0 * (uint32_t)a.S);
+    u.first = a.S - u.xl0;
+    u.mask1 = u.first >= 16 ? 0xffffu : (1u << u.first) - 1u;
+    rows_cursor_row(a, u, max(y0 - 1, 0));
+    RowsRow up, mid, dn;
+    rows_process(a, in, u, y0 - 1, lane, up);
+    rows_process(a, in, u, y0, lane, mid);
+    for (int32_t y = y0; y < y1; ++y) {
+        rows_process(a, in, u, y + 1, lane, dn);
+        uint32_t nw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            nw[q] = rule4_bb(a.rule.lut, up.h[q] + mid.h[q] + dn.h[q], mid.d[q]) & mid.m[q];
+        rows_store(out, (int64_t)y * a.n + u.x0, (int64_t)(y + 1) * a.n, u.x0, lane, nw);
+        up = mid;
+        mid = dn;
+    }
+}
+
 int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                    uint32_t survive, cudaStream_t st)
 {
@@ -314,6 +532,27 @@ int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
         make_rule(birth, survive, &a.rule);
         const int64_t grid = (a.warps + 3) / 4;
         bb_fast_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
+        FR_CUDA(cudaGetLastError());
+        return FR_OK;
+    }
+    if (f->dim == 2 && f->bb.S >= 16 && f->side >= 16 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+        const BBPlan &p = f->bb;
+        BBRowsArgs a;
+        a.n = (int32_t)f->side;
+        a.total = (int64_t)f->side * f->side;
+        a.S = p.S;
+        a.C = p.C;
+        a.sdiv = make_div((uint32_t)p.S);
+        a.local_bits = p.local_bits;
+        a.coarse_bits = p.coarse_bits;
+        a.rows = 64;
+        // strip sx writes up to cell 480 sx + 512 - k (k < 16) and the head
+        // of strip 0 from cell 0: ceil((n - 16) / 480) + 1 strips cover a row
+        a.strips_x = (a.n > 496) ? (a.n - 496 + 479) / 480 + 1 : 1;
+        a.warps = (int64_t)a.strips_x * ((a.n + a.rows - 1) / a.rows);
+        make_rule(birth, survive, &a.rule);
+        const int64_t grid = (a.warps + 3) / 4;
+        bb_rows_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
         FR_CUDA(cudaGetLastError());
         return FR_OK;
     }

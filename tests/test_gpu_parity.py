@@ -295,6 +295,36 @@ def test_bb_vectorised_path_with_garbage(P, fam, r):
         assert np.array_equal(out.cpu().numpy(), o.bb_step(box, steps=steps)), steps
 
 
+@pytest.mark.parametrize("fam,r", [(W.CARPET, 5), (W.CARPET, 6), (W.VICSEK, 6), (W.H_FRACTAL, 5), (W.X_FRACTAL, 6),
+                                   (W.TRIANGLE, 7), (W.TRIANGLE_MIRRORED, 8)],
+                         ids=lambda v: getattr(v, "name", str(v)))
+def test_bb_rows_path_with_garbage(P, fam, r):
+    # 2D boxes whose rows are not 16-byte aligned (local bitmap side >= 16)
+    # take the row-walking path; garbage and non-binary bytes off the fractal
+    g, o = gpu_fr(P, fam, r), ora(fam, r)
+    rng = np.random.default_rng(100 + r)
+    box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
+    b = torch.from_numpy(box).cuda()
+    for steps in (1, 2, 3):
+        out = g.bb_step(b, steps=steps, rule=rule_of(fam))
+        assert np.array_equal(out.cpu().numpy(), o.bb_step(box, rule=oracle_rule(fam), steps=steps)), steps
+    # buffers at unaligned addresses take the generic kernel, with the same result
+    base = torch.zeros(g.box_cells + 16, dtype=torch.uint8, device="cuda")
+    x = base[3:3 + g.box_cells]
+    x.copy_(b)
+    assert np.array_equal(g.bb_step(x, steps=1, rule=rule_of(fam)).cpu().numpy(),
+                          o.bb_step(box, rule=oracle_rule(fam), steps=1))
+
+
+def test_bb_rows_path_carpet_r8_whole_box(P):
+    g, o = gpu_fr(P, W.CARPET, 8), ora(W.CARPET, 8)
+    init = o.init_bernoulli(9, 0.5)
+    box = o.scatter(init)
+    out = g.bb_step(torch.from_numpy(box).cuda(), steps=2)
+    assert np.array_equal(out.cpu().numpy(), o.bb_step(box, steps=2))
+    assert np.array_equal(g.gather(out).cpu().numpy(), o.step(init, steps=2))
+
+
 def test_scatter_gather_roundtrip(P):
     for fam, r in [(W.CARPET, 4), (W.MENGER, 3), (W.TRIANGLE, 9)]:
         g, o = gpu_fr(P, fam, r), ora(fam, r)
