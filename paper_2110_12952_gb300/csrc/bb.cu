@@ -338,10 +338,10 @@ __device__ __forceinline__ uint32_t bits32_at(const uint32_t *__restrict__ bits,
     return __funnelshift_r(__ldg(bits + (pos >> 5)), __ldg(bits + (pos >> 5) + 1), pos & 31);
 }
 
-__device__ __forceinline__ uint32_t coarse_bit(const BBRowsArgs &a, int32_t cx, int32_t cy)
+__device__ __forceinline__ uint32_t coarse_bit(const BBRowsArgs &a, int32_t cx, int32_t cy, int32_t cz)
 {
     if (cx >= a.C) return 0u;
-    const uint32_t c = (uint32_t)cy * (uint32_t)a.C + (uint32_t)cx;
+    const uint32_t c = ((uint32_t)cz * (uint32_t)a.C + (uint32_t)cy) * (uint32_t)a.C + (uint32_t)cx;
     return (__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u;
 }
 
@@ -389,15 +389,18 @@ struct RowsRow {
     uint32_t d[4], m[4], h[4];
 };
 
-// The lane's column constants and the row it stands at: local and coarse
-// row, and the coarse bits of its two possible coarse columns in that
-// coarse row (refreshed when the coarse row changes).
+// The lane's column constants, its plane (3D; plane 0 in 2D) and the row
+// it stands at: local and coarse row, and the coarse bits of its two
+// possible coarse columns there (refreshed when the coarse row changes).
 struct RowsCursor {
     int32_t x0, xl0, cx0;
     uint32_t mask1;       // cells of the first local tile
     int first;            // S - xl0
+    bool live;            // the plane lies inside the box
+    int64_t plane;        // flat offset of the plane (z n^2)
+    int32_t zl, cz;       // local and coarse plane
     int32_t yl, cy;       // of the next row to process
-    uint32_t c1, c2;      // coarse bits of columns cx0, cx0 + 1 in coarse row cy
+    uint32_t c1, c2;      // coarse bits of columns cx0, cx0 + 1 in coarse row cy (and plane cz)
 };
 
 __device__ __forceinline__ void rows_cursor_row(const BBRowsArgs &a, RowsCursor &u, int32_t y)
@@ -405,8 +408,26 @@ __device__ __forceinline__ void rows_cursor_row(const BBRowsArgs &a, RowsCursor 
     const uint32_t cy = divu(a.sdiv, (uint32_t)y);
     u.yl = y - (int32_t)(cy * (uint32_t)a.S);
     u.cy = (int32_t)cy;
-    u.c1 = coarse_bit(a, u.cx0, u.cy);
-    u.c2 = u.first < 16 ? coarse_bit(a, u.cx0 + 1, u.cy) : 0u;   // the second local tile only if the cells reach it
+    u.c1 = coarse_bit(a, u.cx0, u.cy, u.cz);
+    u.c2 = u.first < 16 ? coarse_bit(a, u.cx0 + 1, u.cy, u.cz) : 0u;   // the second local tile only if the cells reach it
+}
+
+// a lane's cursor for strip x0, plane z (z = 0 in 2D), standing at row y
+__device__ __forceinline__ void rows_cursor_init(const BBRowsArgs &a, RowsCursor &u, int32_t x0, int32_t z, int32_t y)
+{
+    u.x0 = x0;
+    const uint32_t cx0 = divu(a.sdiv, (uint32_t)x0);
+    u.cx0 = (int32_t)cx0;
+    u.xl0 = x0 - (int32_t)(cx0 * (uint32_t)a.S);
+    u.first = a.S - u.xl0;
+    u.mask1 = u.first >= 16 ? 0xffffu : (1u << u.first) - 1u;
+    u.live = z >= 0 && z < a.n;
+    const int32_t zc = u.live ? z : 0;
+    u.plane = (int64_t)zc * a.n * a.n;
+    const uint32_t cz = divu(a.sdiv, (uint32_t)zc);
+    u.cz = (int32_t)cz;
+    u.zl = zc - (int32_t)(cz * (uint32_t)a.S);
+    rows_cursor_row(a, u, y);
 }
 
 // masked 0/1 bytes, member bytes and horizontal 3-sums of the lane's cells
@@ -418,8 +439,8 @@ __device__ __forceinline__ void rows_process(const BBRowsArgs &a, const uint8_t 
 {
     const int32_t x0 = u.x0;
     uint32_t raw[4] = {0u, 0u, 0u, 0u}, m16 = 0u;
-    if (y >= 0 && y < a.n) {   // the same in the whole warp
-        const int64_t f = (int64_t)y * a.n + x0;
+    if (u.live && y >= 0 && y < a.n) {   // the same in the whole warp
+        const int64_t f = u.plane + (int64_t)y * a.n + x0;
         const int k = (int)(f & 15);
         const int64_t a0 = f - k;
         const uint4 c = load16_bounded(in, a.total, a0);
@@ -431,7 +452,7 @@ __device__ __forceinline__ void rows_process(const BBRowsArgs &a, const uint8_t 
         if (lane == 31) nx = load16_bounded(in, a.total, a0 + 16);
         const uint32_t w[8] = {c.x, c.y, c.z, c.w, nx.x, nx.y, nx.z, nx.w};
         bytes16_at(w, k, raw);
-        const uint32_t rowbit = (uint32_t)u.yl * (uint32_t)a.S;
+        const uint32_t rowbit = ((uint32_t)u.zl * (uint32_t)a.S + (uint32_t)u.yl) * (uint32_t)a.S;
         m16 = (u.c1 ? bits32_at(a.local_bits, rowbit + (uint32_t)u.xl0) & u.mask1 : 0u) |
               (u.c2 ? (bits32_at(a.local_bits, rowbit) << (u.first & 31)) & 0xffffu : 0u);
         if (++u.yl == a.S && y + 1 < a.n) rows_cursor_row(a, u, y + 1);
@@ -493,13 +514,7 @@ bb_rows_kernel(BBRowsArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
     const int32_t y0 = (int32_t)(wid / a.strips_x) * a.rows;
     const int32_t y1 = min(y0 + a.rows, a.n);
     RowsCursor u;
-    u.x0 = (int32_t)(wid % a.strips_x) * 480 + lane * 16;
-    const uint32_t cx0 = divu(a.sdiv, (uint32_t)u.x0);
-    u.cx0 = (int32_t)cx0;
-    u.xl0 = u.x0 - (int32_t)(cx0 * (uint32_t)a.S);
-    u.first = a.S - u.xl0;
-    u.mask1 = u.first >= 16 ? 0xffffu : (1u << u.first) - 1u;
-    rows_cursor_row(a, u, max(y0 - 1, 0));
+    rows_cursor_init(a, u, (int32_t)(wid % a.strips_x) * 480 + lane * 16, 0, max(y0 - 1, 0));
     RowsRow up, mid, dn;
     rows_process(a, in, u, y0 - 1, lane, up);
     rows_process(a, in, u, y0, lane, mid);
@@ -512,6 +527,73 @@ bb_rows_kernel(BBRowsArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         rows_store(out, (int64_t)y * a.n + u.x0, (int64_t)(y + 1) * a.n, u.x0, lane, nw);
         up = mid;
         mid = dn;
+    }
+}
+
+// The 3D box: a warp takes plane z and a strip of rows y0 .. y1 - 1 of 16
+// cells per lane, and keeps the rows' horizontal sums added over the planes
+// z - 1, z, z + 1 for rows y - 1, y, y + 1 (each step loads row y + 1 of
+// the three planes); their sum is the 27-cell total (<= 27, bytes), the
+// rule a shift of the survival or birth mask per cell.  Neighbouring planes
+// go to consecutive warps, so the rows they share are read from L2.
+__device__ __forceinline__ uint32_t rule27(uint32_t t, uint32_t alive, uint32_t birth, uint32_t live_mask)
+{
+    uint32_t r = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t tj = (t >> (8 * j)) & 0xffu, aj = (alive >> (8 * j)) & 1u;
+        r |= (((aj ? live_mask : birth) >> tj) & 1u) << (8 * j);
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(128)
+bb_rows3_kernel(BBRowsArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wid >= a.warps) return;   // whole warps leave together
+    const int32_t z = (int32_t)(wid % a.n);
+    const int64_t rest = wid / a.n;
+    const int32_t x0 = (int32_t)(rest % a.strips_x) * 480 + lane * 16;
+    const int32_t y0 = (int32_t)(rest / a.strips_x) * a.rows;
+    const int32_t y1 = min(y0 + a.rows, a.n);
+    const uint32_t live_mask = (a.rule.survive << 1) & 0x0ffffffeu, birth = a.rule.birth & 0x07ffffffu;
+    RowsCursor ua, ub, uc;   // planes z - 1, z, z + 1
+    rows_cursor_init(a, ua, x0, z - 1, max(y0 - 1, 0));
+    rows_cursor_init(a, ub, x0, z, max(y0 - 1, 0));
+    rows_cursor_init(a, uc, x0, z + 1, max(y0 - 1, 0));
+    // P: horizontal sums over the three planes; mid: row y of plane z
+    uint32_t pu[4], pm[4], pd[4];
+    RowsRow ra, rb, rc, mid;
+    rows_process(a, in, ua, y0 - 1, lane, ra);
+    rows_process(a, in, ub, y0 - 1, lane, rb);
+    rows_process(a, in, uc, y0 - 1, lane, rc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pu[q] = ra.h[q] + rb.h[q] + rc.h[q];
+    rows_process(a, in, ua, y0, lane, ra);
+    rows_process(a, in, ub, y0, lane, mid);
+    rows_process(a, in, uc, y0, lane, rc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pm[q] = ra.h[q] + mid.h[q] + rc.h[q];
+    for (int32_t y = y0; y < y1; ++y) {
+        rows_process(a, in, ua, y + 1, lane, ra);
+        rows_process(a, in, ub, y + 1, lane, rb);
+        rows_process(a, in, uc, y + 1, lane, rc);
+        uint32_t nw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pd[q] = ra.h[q] + rb.h[q] + rc.h[q];
+            nw[q] = rule27(pu[q] + pm[q] + pd[q], mid.d[q], birth, live_mask) & mid.m[q];
+        }
+        rows_store(out, ub.plane + (int64_t)y * a.n + x0, ub.plane + (int64_t)(y + 1) * a.n, x0, lane, nw);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pu[q] = pm[q];
+            pm[q] = pd[q];
+            mid.d[q] = rb.d[q];
+            mid.m[q] = rb.m[q];
+        }
     }
 }
 
@@ -535,11 +617,11 @@ int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
         FR_CUDA(cudaGetLastError());
         return FR_OK;
     }
-    if (f->dim == 2 && f->bb.S >= 16 && f->side >= 16 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
+    if (f->bb.S >= 16 && f->side >= 16 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
         const BBPlan &p = f->bb;
         BBRowsArgs a;
         a.n = (int32_t)f->side;
-        a.total = (int64_t)f->side * f->side;
+        a.total = (int64_t)f->side * f->side * (f->dim == 3 ? f->side : 1);
         a.S = p.S;
         a.C = p.C;
         a.sdiv = make_div((uint32_t)p.S);
@@ -549,10 +631,14 @@ int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
         // strip sx writes up to cell 480 sx + 512 - k (k < 16) and the head
         // of strip 0 from cell 0: ceil((n - 16) / 480) + 1 strips cover a row
         a.strips_x = (a.n > 496) ? (a.n - 496 + 479) / 480 + 1 : 1;
-        a.warps = (int64_t)a.strips_x * ((a.n + a.rows - 1) / a.rows);
+        if (f->dim == 3) a.rows = 32;
+        a.warps = (int64_t)a.strips_x * ((a.n + a.rows - 1) / a.rows) * (f->dim == 3 ? a.n : 1);
         make_rule(birth, survive, &a.rule);
         const int64_t grid = (a.warps + 3) / 4;
-        bb_rows_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
+        if (f->dim == 3)
+            bb_rows3_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
+        else
+            bb_rows_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
         FR_CUDA(cudaGetLastError());
         return FR_OK;
     }

@@ -316,6 +316,32 @@ def test_bb_rows_path_with_garbage(P, fam, r):
                           o.bb_step(box, rule=oracle_rule(fam), steps=1))
 
 
+@pytest.mark.parametrize("rule", [W.MENGER_B5S45, (0x6, 0x1E)], ids=lambda r: f"B{r[0]:x}S{r[1]:x}")
+def test_bb_rows3_path_menger_r5_with_garbage(P, rule):
+    # 3D boxes with a local bitmap side >= 16 take the plane-walking row path
+    g, o = gpu_fr(P, W.MENGER, 5), ora(W.MENGER, 5)
+    rng = np.random.default_rng(55)
+    box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
+    b = torch.from_numpy(box).cuda()
+    orl = oracle.Rule([i for i in range(27) if (rule[0] >> i) & 1], [i for i in range(27) if (rule[1] >> i) & 1])
+    for steps in (1, 2):
+        out = g.bb_step(b, steps=steps, rule=rule)
+        assert np.array_equal(out.cpu().numpy(), o.bb_step(box, rule=orl, steps=steps)), steps
+
+
+def test_bb_rows3_path_menger_r6_against_compact(P):
+    g, o = gpu_fr(P, W.MENGER, 6), ora(W.MENGER, 6)
+    x = g.init_bernoulli(6, 0.5)
+    init = x.cpu().numpy()
+    out = g.bb_step(g.scatter(x), steps=2, rule=W.MENGER_B5S45)
+    got = g.gather(out).cpu().numpy()
+    assert np.array_equal(got, g.step(x, steps=2, rule=W.MENGER_B5S45).cpu().numpy())
+    # and the compact step itself against the oracle on sampled cells
+    want = o.step(init, rule=oracle.Rule([5], [4, 5]), steps=2)
+    idx = W.sample_omegas(g.cells, 20_000, 7)
+    assert np.array_equal(got[idx], want[idx])
+
+
 def test_bb_rows_path_carpet_r8_whole_box(P):
     g, o = gpu_fr(P, W.CARPET, 8), ora(W.CARPET, 8)
     init = o.init_bernoulli(9, 0.5)
