@@ -240,6 +240,8 @@ extern "C" int fractal_destroy(fractal_t *f)
     fr_paper_aux_free(f);
     free_bb_plan(f->bb);
     cudaFree(f->scratch);
+    cudaFree(f->b3_state[0]);
+    cudaFree(f->b3_state[1]);
     cudaFree(f->bb_scratch);
     cudaFree(f->host_io[0]);
     cudaFree(f->host_io[1]);
@@ -380,6 +382,7 @@ extern "C" int fractal_step(fractal_t *f, const uint8_t *in, uint8_t *out, int64
     }
     int rc = ensure_step_plan(f);
     if (rc) return rc;
+    if (steps > 1 && bit3_plan(f)) return launch_bit3_generations(f, in, out, steps, birth, survive, st);
     if (steps > 1) {
         rc = ensure_buffer(&f->scratch, f->cells, "fractal_step: scratch allocation");
         if (rc) return rc;

@@ -158,14 +158,35 @@ __device__ __forceinline__ uint32_t b3_cube(const uint32_t (&w)[6], const uint32
 // products fall on distinct non-multiples of 8, so nothing carries)
 __device__ __forceinline__ uint32_t b3_nib_bytes(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
 
+// All-zero bit state standing in for absent neighbour tiles.
+__device__ __align__(16) uint32_t g_b3_zero_state[kB3StateWords];
+
+// Box row (y, z) (0..28 each) of a tile from bit-packed states: its cells from the
+// row of the tile (or of the neighbour across the ring) that holds them,
+// its ring bits 0 and 28 from the x-faces of the neighbours in x.  st[q] is
+// the state of the tile in direction q = (dx + 1) + 3 (dy + 1) + 9 (dz + 1)
+// (13: the tile itself; absent tiles: zeros).
+__device__ __forceinline__ uint32_t b3_row_from_state(const uint32_t *const *st, int y, int z)
+{
+    const int dy = (y == 0) ? -1 : (y == 28 ? 1 : 0), dz = (z == 0) ? -1 : (z == 28 ? 1 : 0);
+    const int sy = y - 27 * dy - 1, sz = z - 27 * dz - 1;   // the cell row in the tile that holds it, 0..26
+    const int q = 13 + 3 * dy + 9 * dz;                     // direction (0, dy, dz), 1..25
+    uint32_t w = __ldg(st[q] + sy + 27 * sz);
+    w |= (__ldg(st[q - 1] + kB3StateXH + sz) >> sy) & 1u;            // cell x = -1: face x = 26 of the -x tile
+    w |= ((__ldg(st[q + 1] + kB3StateXL + sz) >> sy) & 1u) << 28;    // cell x = 27: face x = 0 of the +x tile
+    return w;
+}
+
 // B5S45: the rule is B5/S45 (totals 5 for birth, 5 and 6 for survival),
 // evaluated with constants; otherwise the rule of the tile's instance.
 // KW: words per level-1 block (k / 4), or 0 when read from the arguments.
-template <bool MULTI, bool B5S45, int KW>
+// IN_BITS / OUT_BITS: the generation reads / writes the bit-packed states
+// a.b3.sin / a.b3.sout instead of bytes (single-instance launches).
+template <bool MULTI, bool B5S45, int KW, bool IN_BITS = false, bool OUT_BITS = false>
 __global__ void __launch_bounds__(32 * kB3Warps, 4)
 step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     uint32_t *stab = reinterpret_cast<uint32_t *>(smem);
     for (int i = threadIdx.x; i < a.b3.nshared; i += blockDim.x) stab[i] = __ldg(a.tab + i);
     __syncthreads();
@@ -188,65 +209,89 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         const uint32_t both = mb & ms, sonly = ms & ~mb, bonly = mb & ~ms;
         uint8_t *tout = t.out + t.T * KL;
         const uint8_t *tin = t.in + t.T * KL;
-        const bool al4 = (((uintptr_t)t.in) & 3) == 0;
-        // the lane's first block of the tile, loaded while the halo is fetched
-        uint32_t wn[6];
-        if (lane < nblk) b3_load_block<KW>(wn, tin + k * lane, kw, al4);
-        // neighbour tiles by slot
         const int32_t tn = lane < 26 ? __ldg(t.nbr + t.T * a.nbrw + lane) : -1;
-        const uint32_t present = __ballot_sync(0xffffffffu, tn >= 0);
-        if (lane < 26) nbase[lane] = tn >= 0 ? t.in + (int64_t)tn * KL : t.in;
+        if constexpr (IN_BITS) {
+                // 1-2. the states of the tile and its neighbours, by direction; the
+            // rows are read from them as the walk below needs them
+            const uint32_t **st = reinterpret_cast<const uint32_t **>(nbase);
+            const int32_t tq = __shfl_sync(0xffffffffu, tn, lane < 13 ? lane : lane - 1);   // direction lane -> slot
+            if (lane < 27)
+                st[lane] = lane == 13 ? a.b3.sin + t.T * kB3StateWords
+                                      : (tq >= 0 ? a.b3.sin + (int64_t)tq * kB3StateWords : g_b3_zero_state);
+            __syncwarp();
+        } else {
+            const bool al4 = (((uintptr_t)t.in) & 3) == 0;
+            // the lane's first block of the tile, loaded while the halo is fetched
+            uint32_t wn[6];
+            if (lane < nblk) b3_load_block<KW>(wn, tin + k * lane, kw, al4);
+            // neighbour tiles by slot
+            const uint32_t present = __ballot_sync(0xffffffffu, tn >= 0);
+            if (lane < 26) nbase[lane] = tn >= 0 ? t.in + (int64_t)tn * KL : t.in;
 
-        // 1. the halo: the blocks of the neighbour tiles that touch the box's
-        // halo ring, converted like the tile's own blocks, their row pieces
-        // cut to the ring (entries grouped by neighbour slot; absent tiles
-        // are skipped)
-        for (int i = lane; i < kB3BoxWords / 4; i += 32) reinterpret_cast<uint4 *>(box)[i] = make_uint4(0, 0, 0, 0);
-        __syncwarp();
-        for (uint32_t pm = present & 0x3ffffffu; pm; pm &= pm - 1) {
-            const int d = __ffs(pm) - 1;
-            const uint32_t hs = HS[d];
-            const uint8_t *nt = nbase[d];
-            for (int e = (int)(hs & 0xffffu) + lane; e < (int)(hs >> 16); e += 32) {
-                const uint2 en = HE[e];
-                uint32_t w[6];
-                b3_load_block<KW>(w, nt + k * (int)((en.x >> 5) & 1023u), kw, al4);
-                const uint32_t cube = b3_cube<KW>(w, CT, kw);
-                const uint32_t rmask = (en.x >> 15) & 511u, pmask = (en.x >> 24) & 7u, sh2 = en.x >> 27;
-                const int rb = (int)en.y;
+            // 1. the halo: the blocks of the neighbour tiles that touch the box's
+            // halo ring, converted like the tile's own blocks, their row pieces
+            // cut to the ring (entries grouped by neighbour slot; absent tiles
+            // are skipped)
+            for (int i = lane; i < kB3BoxWords / 4; i += 32) reinterpret_cast<uint4 *>(box)[i] = make_uint4(0, 0, 0, 0);
+            __syncwarp();
+            for (uint32_t pm = present & 0x3ffffffu; pm; pm &= pm - 1) {
+                const int d = __ffs(pm) - 1;
+                const uint32_t hs = HS[d];
+                const uint8_t *nt = nbase[d];
+                for (int e = (int)(hs & 0xffffu) + lane; e < (int)(hs >> 16); e += 32) {
+                    const uint2 en = HE[e];
+                    uint32_t w[6];
+                    b3_load_block<KW>(w, nt + k * (int)((en.x >> 5) & 1023u), kw, al4);
+                    const uint32_t cube = b3_cube<KW>(w, CT, kw);
+                    const uint32_t rmask = (en.x >> 15) & 511u, pmask = (en.x >> 24) & 7u, sh2 = en.x >> 27;
+                    const int rb = (int)en.y;
+#pragma unroll
+                    for (int rr = 0; rr < 9; ++rr)
+                        if ((rmask >> rr) & 1u)
+                            atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], (((cube >> (3 * rr)) & pmask) << sh2) >> 2);
+                }
+            }
+            // 2. the tile's cells, a block per lane (the next one loaded ahead),
+            // ORed into their rows
+            for (int j = lane; j < nblk; j += 32) {
+                uint32_t wc[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) wc[q] = wn[q];
+                if (j + 32 < nblk) b3_load_block<KW>(wn, tin + k * (j + 32), kw, al4);
+                const uint32_t cube = b3_cube<KW>(wc, CT, kw);
+                const uint32_t bp = BP[j];
+                const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
 #pragma unroll
                 for (int rr = 0; rr < 9; ++rr)
-                    if ((rmask >> rr) & 1u)
-                        atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], (((cube >> (3 * rr)) & pmask) << sh2) >> 2);
+                    atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], ((cube >> (3 * rr)) & 7u) << sh);
             }
+            __syncwarp();
         }
-        // 2. the tile's cells, a block per lane (the next one loaded ahead),
-        // ORed into their rows
-        for (int j = lane; j < nblk; j += 32) {
-            uint32_t wc[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) wc[q] = wn[q];
-            if (j + 32 < nblk) b3_load_block<KW>(wn, tin + k * (j + 32), kw, al4);
-            const uint32_t cube = b3_cube<KW>(wc, CT, kw);
-            const uint32_t bp = BP[j];
-            const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
-#pragma unroll
-            for (int rr = 0; rr < 9; ++rr)
-                atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], ((cube >> (3 * rr)) & 7u) << sh);
-        }
-        for (int i = lane; i < nbw; i += 32) bits[i] = 0u;
-        __syncwarp();
+        // the result bits start at zero (ORed into below)
+        if constexpr (!OUT_BITS)
+            for (int i = lane; i < nbw; i += 32) bits[i] = 0u;
 
         // 3. the next generation of the inner rows, in place: step z reads
         // row z and writes row z - 1, whose sums are already in registers
         {
-            const uint32_t w0 = lane < kB3Pitch ? box[lane] : 0u;
-            const uint32_t w1 = lane < kB3Pitch ? box[lane + kB3Pitch] : 0u;
+            // box row (lane, z): from the box, or (bit states) from the states
+            const uint32_t *const *st = reinterpret_cast<const uint32_t *const *>(nbase);
+            auto row = [&](int z) -> uint32_t {
+                if (lane >= kB3Pitch) return 0u;
+                if constexpr (IN_BITS) return b3_row_from_state(st, lane, z);
+                else return box[lane + kB3Pitch * z];
+            };
+            const uint32_t w0 = row(0), w1 = row(1);
             B3Q qa = b3_sxy(w0), qb = b3_sxy(w1);
-            uint32_t alive = w1;
+            // rows three planes ahead are in flight (reads from the states
+            // come from L2)
+            uint32_t alive = w1, wa = row(2), wb = row(3), wc = row(4);
 #pragma unroll 3
             for (int z = 2; z < kB3Pitch; ++z) {
-                const uint32_t w = lane < kB3Pitch ? box[lane + kB3Pitch * z] : 0u;
+                const uint32_t w = wa;
+                wa = wb;
+                wb = wc;
+                wc = (z + 3 < kB3Pitch) ? row(z + 3) : 0u;
                 const B3Q qc = b3_sxy(w);
                 const B3T tt = b3_add3(qa, qb, qc);
                 uint32_t nw;
@@ -254,7 +299,22 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
                     nw = b3_eq<5>(tt) | (alive & b3_eq<6>(tt));
                 else
                     nw = b3_rule(tt, alive, both, sonly, bonly);
-                if (lane >= 1 && lane <= 27) box[lane + kB3Pitch * (z - 1)] = nw & 0x0ffffffeu;
+                const bool inner = lane >= 1 && lane <= 27;
+                if constexpr (OUT_BITS) {
+                    // the new row and the row's cells x = 0 and x = 26 into the faces
+                    uint32_t *so = a.b3.sout + t.T * kB3StateWords;
+                    // (positions off the fractal dropped: the next generation reads these rows whole)
+                    if (inner) nw &= stab[a.b3.off_mr + (lane - 1) + 27 * (z - 2)];
+                    if (inner) so[(lane - 1) + 27 * (z - 2)] = nw;
+                    const uint32_t xl = __ballot_sync(0xffffffffu, inner && ((nw >> 1) & 1u)) >> 1;
+                    const uint32_t xh = __ballot_sync(0xffffffffu, inner && ((nw >> 27) & 1u)) >> 1;
+                    if (lane == 0) {
+                        so[kB3StateXL + z - 2] = xl;
+                        so[kB3StateXH + z - 2] = xh;
+                    }
+                } else {
+                    if (inner) box[lane + kB3Pitch * (z - 1)] = nw & 0x0ffffffeu;
+                }
                 qa = qb;
                 qb = qc;
                 alive = w;
@@ -262,31 +322,33 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         }
         __syncwarp();
 
-        // 4. the results: each block's k bits (a table per row piece) into
-        // the tile's bit string, then 16 cells per lane and step to memory
-        for (int j = lane; j < nblk; j += 32) {
-            const uint32_t bp = BP[j];
-            const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
-            uint32_t m = 0u;
+        if constexpr (!OUT_BITS) {
+            // 4. the results: each block's k bits (a table per row piece) into
+            // the tile's bit string, then 16 cells per lane and step to memory
+            for (int j = lane; j < nblk; j += 32) {
+                const uint32_t bp = BP[j];
+                const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
+                uint32_t m = 0u;
 #pragma unroll
-            for (int rr = 0; rr < 9; ++rr)
-                m |= RT[rr * 8 + ((box[rb + rr % 3 + kB3Pitch * (rr / 3)] >> sh) & 7u)];
-            const int b = k * j, wi = b >> 5, s = b & 31;
-            atomicOr(&bits[wi], m << s);
-            if (s + k > 32) atomicOr(&bits[wi + 1], m >> (32 - s));
-        }
-        __syncwarp();
-        if ((((uintptr_t)tout) & 15) == 0) {
-            for (int h = lane; h < (int)(KL / 16); h += 32) {
-                const uint32_t hw = bits[h >> 1] >> (16 * (h & 1));
-                reinterpret_cast<uint4 *>(tout)[h] =
-                    make_uint4(b3_nib_bytes(hw & 0xfu), b3_nib_bytes((hw >> 4) & 0xfu), b3_nib_bytes((hw >> 8) & 0xfu),
-                               b3_nib_bytes((hw >> 12) & 0xfu));
+                for (int rr = 0; rr < 9; ++rr)
+                    m |= RT[rr * 8 + ((box[rb + rr % 3 + kB3Pitch * (rr / 3)] >> sh) & 7u)];
+                const int b = k * j, wi = b >> 5, s = b & 31;
+                atomicOr(&bits[wi], m << s);
+                if (s + k > 32) atomicOr(&bits[wi + 1], m >> (32 - s));
             }
-        } else {
-            for (int c = lane; c < (int)KL; c += 32) tout[c] = (uint8_t)((bits[c >> 5] >> (c & 31)) & 1u);
+            __syncwarp();
+            if ((((uintptr_t)tout) & 15) == 0) {
+                for (int h = lane; h < (int)(KL / 16); h += 32) {
+                    const uint32_t hw = bits[h >> 1] >> (16 * (h & 1));
+                    reinterpret_cast<uint4 *>(tout)[h] =
+                        make_uint4(b3_nib_bytes(hw & 0xfu), b3_nib_bytes((hw >> 4) & 0xfu), b3_nib_bytes((hw >> 8) & 0xfu),
+                                   b3_nib_bytes((hw >> 12) & 0xfu));
+                }
+            } else {
+                for (int c = lane; c < (int)KL; c += 32) tout[c] = (uint8_t)((bits[c >> 5] >> (c & 31)) & 1u);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 

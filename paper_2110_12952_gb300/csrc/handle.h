@@ -20,9 +20,12 @@ struct Bit3Args {
     int off_bp = 0;        // block j -> box row of its first row | bit shift << 16: k^2 words
     int off_hs = 0;        // neighbour slot -> its halo entries: first | end << 16, 26 words
     int off_he = 0;        // halo entries (two words each, grouped by slot)
+    int off_mr = 0;        // members of inner row (y, z) (bits 1..27), 729 words: masks rows of bit states
     int nshared = 0;       // words copied to shared memory
     int off_warp = 0;      // byte offset of warp 0's area in shared memory
     int warp_bytes = 0;    // shared memory per warp (box, pointers, result bits)
+    const uint32_t *sin = nullptr;   // multi-generation runs: bit-packed input state (kB3StateWords per tile)
+    uint32_t *sout = nullptr;        // and output state, or null
 };
 
 // Tiled compact step (Sec. 3 stencil procedure, done per subtree).
@@ -127,6 +130,7 @@ struct fractal {
     fr::StepPlan plan;
     fr::BBPlan bb;
     uint8_t *scratch = nullptr;      // k^r bytes, ping-pong for steps > 1
+    uint32_t *b3_state[2] = {nullptr, nullptr};  // bit3 plans, steps > 1: bit-packed tile states (ping-pong)
     uint8_t *bb_scratch = nullptr;   // n^dim bytes, ping-pong for BB steps > 1
     uint8_t *host_io[2] = {nullptr, nullptr};  // device buffers of run_host
     fr::HostPipe pipe;                          // run_host's chunked pipeline
@@ -176,13 +180,19 @@ void free_bb_plan(BBPlan &p);
 
 int launch_step_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
                      uint32_t survive, cudaStream_t st);
-// One generation of the tiles 0 .. ntiles-1 of the buffer `in` (tile T at
-// cell T k^L) with the neighbour table `nbr` (ntiles rows, indices of tiles
-// of the same buffer, which holds readable_cells cells), into `out`.
 // One generation of the instance's tiles T0 .. T1 - 1 only (the others are
 // read as neighbours, not written).
 int launch_step_range(fractal *f, const uint8_t *in, uint8_t *out, int64_t T0, int64_t T1, uint32_t birth,
                       uint32_t survive, cudaStream_t st);
+// Whether the handle's step plan is the bit3 policy; `steps` >= 2
+// generations of such a plan with the state bit-packed between them (the
+// first generation reads bytes, the last writes them).
+bool bit3_plan(const fractal *f);
+int launch_bit3_generations(fractal *f, const uint8_t *in, uint8_t *out, int64_t steps, uint32_t birth,
+                            uint32_t survive, cudaStream_t st);
+// One generation of the tiles 0 .. ntiles-1 of the buffer `in` (tile T at
+// cell T k^L) with the neighbour table `nbr` (ntiles rows, indices of tiles
+// of the same buffer, which holds readable_cells cells), into `out`.
 int launch_step_tiles(fractal *f, const uint8_t *in, uint8_t *out, const int32_t *nbr, int64_t ntiles,
                       int64_t readable_cells, uint32_t birth, uint32_t survive, cudaStream_t st);
 int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,

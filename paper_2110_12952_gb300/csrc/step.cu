@@ -204,13 +204,14 @@ static int bit3_shared_words(const fractal *f)
 {
     std::vector<uint32_t> hs;
     const size_t nhe = bit3_halo(f, hs).size();
-    return (int)((f->k / 4) * 16 + 72 + f->k * f->k + 26 + 2 + nhe);
+    return (int)((f->k / 4) * 16 + 72 + f->k * f->k + 26 + 2 + nhe + 729);
 }
 static int bit3_warp_bytes(const fractal *f) { return kB3OffBits + (int)round16(((int64_t)f->k * f->k * f->k + 7) / 8); }
 
 // The bit3 tables, in the order of Bit3Args: cube bits of each nibble of
 // each word of a block; result bits of each 3-bit row piece; box row and bit
-// shift of each block of a tile; the halo entries by neighbour slot.  A halo
+// shift of each block of a tile; the halo entries by neighbour slot; the
+// member bits of each inner box row.  A halo
 // entry is slot | block index << 5 | rows in the ring << 15 | cells of a row
 // piece in the ring << 24 | (box bit of the piece's first cell + 2) << 27,
 // then the box row of the block's first row (which may lie outside the box).
@@ -253,6 +254,16 @@ static std::vector<uint32_t> bit3_tables(const fractal *f, Bit3Args &b)
     while (t.size() % 2) t.push_back(0);
     b.off_he = (int)t.size();
     t.insert(t.end(), he.begin(), he.end());
+    b.off_mr = (int)t.size();
+    for (int z = 0; z < 27; ++z)
+        for (int y = 0; y < 27; ++y) {
+            uint32_t m = 0;
+            for (int x = 0; x < 27; ++x) {
+                const int c[3] = {x, y, z};
+                if (host_nu(f, c, 3) >= 0) m |= 1u << (x + 1);
+            }
+            t.push_back(m);
+        }
     b.nshared = (int)t.size();
     return t;
 }
@@ -977,8 +988,21 @@ static int configure(StepPlan &p, int num_sms)
     return FR_OK;
 }
 
-template <bool MULTI, bool B5S45, int KW>
+template <bool MULTI, bool B5S45, int KW, bool IN_BITS, bool OUT_BITS>
 __global__ void step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out);
+
+// every instantiation of the bit3 kernel may use the opt-in shared memory
+template <bool B5S45, int KW>
+static int bit3_allow_smem(int optin)
+{
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, B5S45, KW, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, B5S45, KW, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, B5S45, KW, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, B5S45, KW, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    if (!B5S45)
+        FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<true, false, KW, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    return FR_OK;
+}
 
 // bit3 mode: eight tiles (warps) per block
 static int configure_bit3(StepPlan &p, int num_sms)
@@ -990,12 +1014,12 @@ static int configure_bit3(StepPlan &p, int num_sms)
         set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
         return FR_EINVAL;
     }
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<true, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<false, true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaFuncSetAttribute(step_bit3_kernel<true, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_bit3_kernel<false, false, 0>, p.block, p.smem));
+    int rc = bit3_allow_smem<false, 0>(optin);
+    if (!rc) rc = bit3_allow_smem<true, 0>(optin);
+    if (!rc) rc = bit3_allow_smem<false, 5>(optin);
+    if (!rc) rc = bit3_allow_smem<true, 5>(optin);
+    if (rc) return rc;
+    FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_bit3_kernel<false, false, 0, false, false>, p.block, p.smem));
     if (per_sm < 1) {
         set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
         return FR_EINVAL;
@@ -2488,12 +2512,14 @@ static int dispatch(const fractal *f, const StepArgs &a, int grid, const uint8_t
         // and the Menger sponge's five words per block with constants
         grid = (int)std::min<int64_t>(grid, (a.NT + kB3Warps - 1) / kB3Warps);
         const bool b5s45 = !MULTI && a.rule.birth == (1u << 5) && a.rule.survive == ((1u << 4) | (1u << 5));
-        if (p.b3.k != 20)
-            step_bit3_kernel<MULTI, false, 0><<<grid, p.block, p.smem, st>>>(a, in, out);
+        if (p.b3.k != 20 && b5s45)
+            step_bit3_kernel<MULTI, !MULTI, 0, false, false><<<grid, p.block, p.smem, st>>>(a, in, out);
+        else if (p.b3.k != 20)
+            step_bit3_kernel<MULTI, false, 0, false, false><<<grid, p.block, p.smem, st>>>(a, in, out);
         else if (b5s45)
-            step_bit3_kernel<MULTI, !MULTI, 5><<<grid, p.block, p.smem, st>>>(a, in, out);
+            step_bit3_kernel<MULTI, !MULTI, 5, false, false><<<grid, p.block, p.smem, st>>>(a, in, out);
         else
-            step_bit3_kernel<MULTI, false, 5><<<grid, p.block, p.smem, st>>>(a, in, out);
+            step_bit3_kernel<MULTI, false, 5, false, false><<<grid, p.block, p.smem, st>>>(a, in, out);
         FR_CUDA(cudaGetLastError());
         return FR_OK;
     }
@@ -2562,6 +2588,62 @@ int launch_step_tiles(fractal *f, const uint8_t *in, uint8_t *out, const int32_t
     a.nbr = nbr;
     const int grid = (int)std::min<int64_t>((int64_t)f->plan.per_sm * f->num_sms, ntiles);
     return dispatch<false>(f, a, grid, in, out, st);
+}
+
+bool bit3_plan(const fractal *f) { return f->plan.pos && f->plan.mode == kModeBit3; }
+
+// one generation of a bit3 plan reading / writing bit-packed states
+template <bool IB, bool OB>
+static int launch_bit3_mode(const fractal *f, const StepArgs &a, const uint8_t *in, uint8_t *out, cudaStream_t st)
+{
+    const StepPlan &p = f->plan;
+    const int grid = (int)std::min<int64_t>(p.grid, (a.NT + kB3Warps - 1) / kB3Warps);
+    const bool b5s45 = a.rule.birth == (1u << 5) && a.rule.survive == ((1u << 4) | (1u << 5));
+    if (p.b3.k != 20 && b5s45)
+        step_bit3_kernel<false, true, 0, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+    else if (p.b3.k != 20)
+        step_bit3_kernel<false, false, 0, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+    else if (b5s45)
+        step_bit3_kernel<false, true, 5, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+    else
+        step_bit3_kernel<false, false, 5, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+    FR_CUDA(cudaGetLastError());
+    return FR_OK;
+}
+
+int launch_bit3_generations(fractal *f, const uint8_t *in, uint8_t *out, int64_t steps, uint32_t birth,
+                            uint32_t survive, cudaStream_t st)
+{
+    if (!bit3_plan(f) || steps < 2) {
+        set_error(FR_EINVAL, "fractal_step: bit-packed generations need a bit3 plan and two generations or more");
+        return FR_EINVAL;
+    }
+    const size_t bytes = (size_t)f->plan.NT * kB3StateWords * sizeof(uint32_t);
+    for (int i = 0; i < 2; ++i) {
+        if (f->b3_state[i]) continue;
+        cudaError_t e = cudaMalloc(&f->b3_state[i], bytes);
+        if (e != cudaSuccess) {
+            f->b3_state[i] = nullptr;
+            return cuda_fail(e, "fractal_step: bit-state allocation");
+        }
+    }
+    StepArgs a;
+    fill_args(f, a);
+    make_rule(birth, survive, &a.rule);
+    a.b3.sin = nullptr;
+    a.b3.sout = f->b3_state[0];
+    int rc = launch_bit3_mode<false, true>(f, a, in, out, st);
+    for (int64_t g = 2; g < steps && !rc; ++g) {
+        a.b3.sin = f->b3_state[(g - 2) & 1];
+        a.b3.sout = f->b3_state[(g - 1) & 1];
+        rc = launch_bit3_mode<true, true>(f, a, in, out, st);
+    }
+    if (!rc) {
+        a.b3.sin = f->b3_state[(steps - 2) & 1];
+        a.b3.sout = nullptr;
+        rc = launch_bit3_mode<true, false>(f, a, in, out, st);
+    }
+    return rc;
 }
 
 int launch_step_multi(const fractal *cls, const InstDesc *descs, const int32_t *tile_inst,

@@ -3,7 +3,8 @@ warp per tile, box rows as bit-sliced words) against the oracle: the rule
 evaluated with constants (B5/S45) and in general, non-binary input, other 3D
 tables whose replica counts are multiples of 4 (and a permuted replica
 order), buffers at unaligned addresses, tile ranges (the chunked host call),
-a batch of instances with different rules, and the plan it is chosen for."""
+a batch of instances with different rules, the bit-packed state between the
+generations of a multi-generation call, and the plan it is chosen for."""
 import numpy as np
 import pytest
 import torch
@@ -125,3 +126,16 @@ def test_batch_with_different_rules(P):
     for g, o, init, y, rule in keep:
         assert np.array_equal(y.cpu().numpy(), o.step(init, rule=orule(rule), steps=5))
     batch.close()
+
+
+@pytest.mark.parametrize("fam,r", [(W.MENGER, 4), (EDGES12, 4), (MENGER_REV, 5)], ids=lambda v: getattr(v, "name", str(v)))
+@pytest.mark.parametrize("rule", [W.MENGER_B5S45, (0x6, 0x1E)], ids=lambda r: f"B{r[0]:x}S{r[1]:x}")
+def test_bit_packed_generations(P, fam, r, rule):
+    # steps >= 2: the first generation writes bit-packed tile states, the
+    # ones between read and write them, the last writes bytes
+    g, o = pair(P, fam, r)
+    raw = nonbinary(o.cells, 21)
+    x = torch.from_numpy(raw).cuda()
+    for steps in (2, 3, 5):
+        got = g.step(x, steps=steps, rule=rule).cpu().numpy()
+        assert np.array_equal(got, o.step(raw, rule=orule(rule), steps=steps)), steps
