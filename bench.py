@@ -701,6 +701,19 @@ def temporal_compare(g, x, y, single_ms, peak):
                     "the roofline of single generations is 2 B per update"}
 
 
+def multigen_compare(g, x, y, ms_single, gens=50):
+    """One call of `gens` generations (bit3 policy: the state stays bit-packed
+    between the first and the last generation), timed three times."""
+    import torch
+    g.step(x, out=y, steps=gens)
+    ts = time_steps(lambda: g.step(x, out=y, steps=gens), 3, 1)
+    ms = statistics.median(ts)
+    return {"generations_per_call": gens, "ms_per_call": ms, "ms_per_generation": ms / gens,
+            "updates_per_s": g.cells * gens / (ms / 1e3), "speedup_vs_single_generation": ms_single / (ms / gens),
+            "note": "first generation bytes -> bit-packed tile states, the ones between states -> states, "
+                    "the last states -> bytes; per-generation bytes are not comparable with the 2 B/update roofline"}
+
+
 def _tb_smem(L):
     # shared memory of the temporal-blocking plan at tile depth L (carpet)
     r16 = lambda v: (v + 15) // 16 * 16
@@ -739,6 +752,8 @@ def others_compare(args, W):
                "l2_flush": small}
         if inst.family.name == "carpet":
             res["temporal_blocking"] = temporal_compare(g, x, y, ms, peak)
+        if inst.family.name == "menger":
+            res["bit_packed_generations"] = multigen_compare(g, x, y, ms)
         if g.box_cells <= 4 * 2**30:
             box = g.scatter(x)
             del x, y
