@@ -26,6 +26,11 @@
 // (the first while the halo is fetched); with a small shared-memory area per
 // warp, 32 warps fit on an SM to hide the latency.  The results are gathered
 // into a bit string in omega order and leave as whole 16-byte words.
+//
+// A call of several generations keeps the state bit-packed between them
+// (bit3_layout.h: per tile its inner rows and its two x-faces): the first
+// generation does 1-3 and writes rows and faces, the last reads the rows in
+// 3 from the states and does 4, the ones between do neither conversion.
 #pragma once
 
 #include <stdint.h>
