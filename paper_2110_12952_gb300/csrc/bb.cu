@@ -8,9 +8,13 @@
 // Both are precomputed bitmaps (about sqrt of the box each), so a cell's
 // membership costs two divisions by s^Lb and two bit look-ups.
 //
-// Each CTA stages a tile of the box plus a one-cell halo in shared memory,
-// one byte per cell (bit 0 = alive member, bit 1 = member), then applies the
-// rule from there.
+// Three kernels: rows of 16 cells per lane walked down by a warp for 2D
+// boxes with s = 2 and aligned rows (bb_fast_kernel) and for other 2D and 3D
+// boxes whose local bitmap side is at least 16 (bb_rows_kernel,
+// bb_rows3_kernel); otherwise (small boxes, buffers not 16-byte aligned)
+// each CTA stages a tile of the box plus a one-cell halo in shared memory,
+// one byte per cell (bit 0 = alive member, bit 1 = member), and applies the
+// rule from there (bb_kernel).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
