@@ -279,12 +279,28 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         // 3. the next generation of the inner rows, in place: step z reads
         // row z and writes row z - 1, whose sums are already in registers
         {
-            // box row (lane, z): from the box, or (bit states) from the states
+            // box row (lane, z): from the box, or (bit states) from the states;
+            // in the planes 1..27 a lane's row and its ring bits come from the
+            // same three states, fixed for the tile
             const uint32_t *const *st = reinterpret_cast<const uint32_t *const *>(nbase);
+            const int dyl = lane == 0 ? -1 : (lane == 28 ? 1 : 0), syl = lane - 27 * dyl - 1;
+            const uint32_t *p0 = nullptr, *pm = nullptr, *pp = nullptr;
+            if constexpr (IN_BITS) {
+                if (lane < kB3Pitch) {
+                    p0 = st[13 + 3 * dyl] + syl;
+                    pm = st[12 + 3 * dyl] + kB3StateXH;
+                    pp = st[14 + 3 * dyl] + kB3StateXL;
+                }
+            }
             auto row = [&](int z) -> uint32_t {
                 if (lane >= kB3Pitch) return 0u;
-                if constexpr (IN_BITS) return b3_row_from_state(st, lane, z);
-                else return box[lane + kB3Pitch * z];
+                if constexpr (IN_BITS) {
+                    if (z == 0 || z == kB3Pitch - 1) return b3_row_from_state(st, lane, z);
+                    const int sz = z - 1;
+                    return __ldg(p0 + 27 * sz) | ((__ldg(pm + sz) >> syl) & 1u) | (((__ldg(pp + sz) >> syl) & 1u) << 28);
+                } else {
+                    return box[lane + kB3Pitch * z];
+                }
             };
             const uint32_t w0 = row(0), w1 = row(1);
             B3Q qa = b3_sxy(w0), qb = b3_sxy(w1);
