@@ -18,6 +18,11 @@ CORNERS8 = W.Family("corners8", 8, 3, 3, tuple((x, y, z) for z in (0, 2) for y i
 EDGES12 = W.Family("edges12", 12, 3, 3, tuple((x, y, z) for z in range(3) for y in range(3) for x in range(3)
                                               if [x, y, z].count(1) == 1))
 MENGER_REV = W.Family("menger_rev", 20, 3, 3, tuple(reversed(W.MENGER.table())))
+# the extremes of k: one word per block (4 cells) and six (24 cells; its
+# tables and boxes need more than 48 KB of shared memory per block)
+FOUR4 = W.Family("four4", 4, 3, 3, ((0, 0, 0), (2, 0, 0), (1, 2, 0), (1, 1, 2)))
+DENSE24 = W.Family("dense24", 24, 3, 3, tuple((x, y, z) for z in range(3) for y in range(3) for x in range(3)
+                                              if (x, y, z) not in ((1, 1, 1), (0, 1, 1), (1, 0, 2))))
 
 RULES = [W.MENGER_B5S45, (1 << 4, 1 << 4), (0x6, 0x1E), (0x7FFE000, 0x7FFE000), (0x2, 0x3), (0, 0)]
 
@@ -73,7 +78,8 @@ def test_rules_on_nonbinary_input(P, rule):
     assert np.array_equal(got, o.step(init, rule=orule(rule), steps=6))
 
 
-@pytest.mark.parametrize("fam,r", [(CORNERS8, 5), (EDGES12, 4), (MENGER_REV, 4), (W.MENGER, 3), (W.MENGER, 5)],
+@pytest.mark.parametrize("fam,r", [(CORNERS8, 5), (EDGES12, 4), (MENGER_REV, 4), (W.MENGER, 3), (W.MENGER, 5),
+                                   (FOUR4, 6), (DENSE24, 4)],
                          ids=lambda v: getattr(v, "name", str(v)))
 def test_tables_and_sizes(P, fam, r):
     g, o = pair(P, fam, r)
@@ -139,3 +145,13 @@ def test_bit_packed_generations(P, fam, r, rule):
     for steps in (2, 3, 5):
         got = g.step(x, steps=steps, rule=rule).cpu().numpy()
         assert np.array_equal(got, o.step(raw, rule=orule(rule), steps=steps)), steps
+
+
+@pytest.mark.parametrize("fam,r", [(EDGES12, 5), (CORNERS8, 5), (DENSE24, 5)], ids=lambda v: getattr(v, "name", str(v)))
+def test_bb_rows3_other_tables(P, fam, r):
+    # the 3D row kernel of the bounding-box step on tables other than the Menger sponge's
+    g, o = pair(P, fam, r)
+    rng = np.random.default_rng(r)
+    box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
+    got = g.bb_step(torch.from_numpy(box).cuda(), steps=2, rule=(0x6, 0x1E)).cpu().numpy()
+    assert np.array_equal(got, o.bb_step(box, rule=orule((0x6, 0x1E)), steps=2))
