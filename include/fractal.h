@@ -148,7 +148,12 @@ int fractal_init_bernoulli(const fractal_t *f, uint8_t *state_dev,
  * the rule.  in_dev and out_dev are k^r-byte compact states that must not
  * overlap; in_dev is never written.  steps = 0 copies (normalised to 0/1).
  * For steps > 1 the library ping-pongs through its own scratch buffer of k^r
- * bytes, allocated on first need and kept until fractal_destroy. */
+ * bytes, allocated on first need and kept until fractal_destroy.  When the
+ * step's plan is the bit3 policy (3D fractals with s = 3 and k a multiple of
+ * 4 at tile depth 3, fractal_plan_info policy 15), steps > 1 keep the state
+ * bit-packed between the first and the last generation instead, in two
+ * buffers of 3136 bytes per level-3 tile (k^(r-3) tiles), likewise allocated
+ * on first need and kept until fractal_destroy; the result is the same. */
 int fractal_step(fractal_t *f, const uint8_t *in_dev, uint8_t *out_dev,
                  int64_t steps, uint32_t birth_mask, uint32_t survive_mask,
                  void *stream);
@@ -271,10 +276,10 @@ int fractal_set_temporal_blocking(fractal_t *f, int generations, int tile_levels
  * box, 10: the triangle's 81-cell units with taps, 11 / 12: the carpet's /
  * Vicsek fractal's level-2 units summed by rows, 13: the Vicsek fractal's
  * level-3 units summed in omega order, 14: a 3D tile's box summed by whole
- * rows, then gathered in omega order), the tile depth L,
- * threads per block, blocks per launch, dynamic shared memory bytes per
- * block, input pipeline stages, and resident blocks per SM.  1 <= n <= 7,
- * else FR_EINVAL. */
+ * rows, then gathered in omega order, 15: a 3D tile of depth 3 per warp,
+ * its box bit-sliced), the tile depth L, threads per block, blocks per
+ * launch, dynamic shared memory bytes per block, input pipeline stages (0:
+ * none), and resident blocks per SM.  1 <= n <= 7, else FR_EINVAL. */
 int fractal_plan_info(const fractal_t *f, int32_t *info, int n);
 
 /* Autotuner of fractal_step: times one generation from in_dev into out_dev
