@@ -128,11 +128,13 @@ __device__ __forceinline__ uint32_t b3_rule(const B3T &t, uint32_t alive, uint32
 // The words of the level-1 block at src (k bytes, k = 4 kw): aligned
 // 4-byte loads, or bytes where the buffer is not 4-byte aligned.
 template <int KW>
-__device__ __forceinline__ void b3_load_block(uint32_t (&w)[6], const uint8_t *src, int kw, bool al4)
+__device__ __forceinline__ void b3_load_block(uint32_t (&w)[6], const uint8_t *src, int kw, bool al4,
+                                              uint32_t wmask = 0x3fu)
 {
 #pragma unroll
     for (int q = 0; q < (KW ? KW : 6); ++q) {
-        if (KW || q < kw) {
+        w[q] = 0u;
+        if ((KW || q < kw) && ((wmask >> q) & 1u)) {
             if (al4)
                 w[q] = __ldg(reinterpret_cast<const uint32_t *>(src) + q);
             else
@@ -143,15 +145,16 @@ __device__ __forceinline__ void b3_load_block(uint32_t (&w)[6], const uint8_t *s
 }
 
 // The 27-bit cube of a block (bit x + 3y + 9z for its cell at (x, y, z))
-// from its words: bit 7 of each nonzero byte, bits 7, 15, 23, 31 gathered
-// into a nibble by a carry-free multiply, a table per word and nibble.
+// from its words (those in wmask): bit 7 of each nonzero byte, bits 7, 15,
+// 23, 31 gathered into a nibble by a carry-free multiply, a table per word
+// and nibble.
 template <int KW>
-__device__ __forceinline__ uint32_t b3_cube(const uint32_t (&w)[6], const uint32_t *CT, int kw)
+__device__ __forceinline__ uint32_t b3_cube(const uint32_t (&w)[6], const uint32_t *CT, int kw, uint32_t wmask = 0x3fu)
 {
     uint32_t cube = 0u;
 #pragma unroll
     for (int q = 0; q < (KW ? KW : 6); ++q) {
-        if (KW || q < kw) {
+        if ((KW || q < kw) && ((wmask >> q) & 1u)) {
             const uint32_t c = (((w[q] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w[q]) & 0x80808080u;
             cube |= CT[q * 16 + ((c * 0x00204081u) >> 28)];
         }
@@ -241,13 +244,13 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
             __syncwarp();
             for (uint32_t pm = present & 0x3ffffffu; pm; pm &= pm - 1) {
                 const int d = __ffs(pm) - 1;
-                const uint32_t hs = HS[d];
+                const uint32_t hs = HS[d], wm = hs >> 26;   // the words holding the cells this direction needs
                 const uint8_t *nt = nbase[d];
-                for (int e = (int)(hs & 0xffffu) + lane; e < (int)(hs >> 16); e += 32) {
+                for (int e = (int)(hs & 0x1fffu) + lane; e < (int)((hs >> 13) & 0x1fffu); e += 32) {
                     const uint2 en = HE[e];
                     uint32_t w[6];
-                    b3_load_block<KW>(w, nt + k * (int)((en.x >> 5) & 1023u), kw, al4);
-                    const uint32_t cube = b3_cube<KW>(w, CT, kw);
+                    b3_load_block<KW>(w, nt + k * (int)((en.x >> 5) & 1023u), kw, al4, wm);
+                    const uint32_t cube = b3_cube<KW>(w, CT, kw, wm);
                     const uint32_t rmask = (en.x >> 15) & 511u, pmask = (en.x >> 24) & 7u, sh2 = en.x >> 27;
                     const int rb = (int)en.y;
 #pragma unroll
@@ -268,7 +271,8 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
                 const int rb = (int)(bp & 0xffffu), sh = (int)(bp >> 16);
 #pragma unroll
                 for (int rr = 0; rr < 9; ++rr)
-                    atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], ((cube >> (3 * rr)) & 7u) << sh);
+                    if ((a.b3.rowset >> rr) & 1u)   // rows of the cube that hold members
+                        atomicOr(&box[rb + rr % 3 + kB3Pitch * (rr / 3)], ((cube >> (3 * rr)) & 7u) << sh);
             }
             __syncwarp();
         }
@@ -352,7 +356,8 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
                 uint32_t m = 0u;
 #pragma unroll
                 for (int rr = 0; rr < 9; ++rr)
-                    m |= RT[rr * 8 + ((box[rb + rr % 3 + kB3Pitch * (rr / 3)] >> sh) & 7u)];
+                    if ((a.b3.rowset >> rr) & 1u)
+                        m |= RT[rr * 8 + ((box[rb + rr % 3 + kB3Pitch * (rr / 3)] >> sh) & 7u)];
                 const int b = k * j, wi = b >> 5, s = b & 31;
                 atomicOr(&bits[wi], m << s);
                 if (s + k > 32) atomicOr(&bits[wi + 1], m >> (32 - s));

@@ -16,9 +16,10 @@ namespace fr {
 // as word offsets into the plan's `pos` array, all copied to shared memory.
 struct Bit3Args {
     int k = 0;             // cells per level-1 block (a multiple of 4)
+    uint32_t rowset = 0;   // rows dy + 3 dz of a block's 3x3x3 cube that hold members
     int off_rt = 0;        // result bits of row piece (row, 3 bits): 9 x 8 words
     int off_bp = 0;        // block j -> box row of its first row | bit shift << 16: k^2 words
-    int off_hs = 0;        // neighbour slot -> its halo entries: first | end << 16, 26 words
+    int off_hs = 0;        // neighbour slot -> its halo entries: first | end << 13 | words needed << 26, 26 words
     int off_he = 0;        // halo entries (two words each, grouped by slot)
     int off_mr = 0;        // members of inner row (y, z) (bits 1..27), 729 words: masks rows of bit states
     int nshared = 0;       // words copied to shared memory

@@ -159,7 +159,9 @@ static bool bit3_ok(const fractal *f, int L)
 }
 
 // halo entries of a 3D fractal with s = 3 at three levels: per neighbour
-// direction, the blocks of that tile which touch the box's one-cell ring
+// direction, the blocks of that tile which touch the box's one-cell ring,
+// and (in hs) the words of a block that hold the cells those blocks
+// contribute (the same for every block of a direction)
 static std::vector<uint32_t> bit3_halo(const fractal *f, std::vector<uint32_t> &hs)
 {
     std::vector<uint32_t> he;
@@ -169,6 +171,7 @@ static std::vector<uint32_t> bit3_halo(const fractal *f, std::vector<uint32_t> &
         const int dir[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
         const int slot = q < 13 ? q : q - 1;
         const uint32_t first = (uint32_t)(he.size() / 2);
+        uint32_t words = 0;
         int lo[3], hi[3];
         for (int a = 0; a < 3; ++a) {
             lo[a] = dir[a] < 0 ? 8 : 0;   // the neighbour's blocks next to this tile
@@ -190,12 +193,17 @@ static std::vector<uint32_t> bit3_halo(const fractal *f, std::vector<uint32_t> &
                     }
                     for (int x0 = 0; x0 < 3; ++x0)
                         if (o[0] + x0 >= 0 && o[0] + x0 <= 28) pmask |= 1u << x0;
+                    for (int rr = 0; rr < 9; ++rr)
+                        for (int x0 = 0; x0 < 3; ++x0) {
+                            const int h = f->dev.hinv[x0 + 3 * rr];
+                            if (((rmask >> rr) & 1) && ((pmask >> x0) & 1) && h >= 0) words |= 1u << (h / 4);
+                        }
                     const int rowbase = o[1] + kB3Pitch * o[2];
                     he.push_back((uint32_t)slot | (uint32_t)jb << 5 | rmask << 15 | pmask << 24 |
                                  (uint32_t)(o[0] + 2) << 27);
                     he.push_back((uint32_t)rowbase);
                 }
-        hs[slot] = first | (uint32_t)(he.size() / 2) << 16;
+        hs[slot] = first | (uint32_t)(he.size() / 2) << 13 | words << 26;
     }
     return he;
 }
@@ -231,11 +239,13 @@ static std::vector<uint32_t> bit3_tables(const fractal *f, Bit3Args &b)
             t.push_back(m);
         }
     b.off_rt = (int)t.size();
+    b.rowset = 0;
     for (int rr = 0; rr < 9; ++rr)             // row rr = dy + 3 dz of the cube
         for (int piece = 0; piece < 8; ++piece) {
             uint32_t m = 0;
             for (int x = 0; x < 3; ++x) {
                 const int h = f->dev.hinv[x + 3 * rr];
+                if (h >= 0) b.rowset |= 1u << rr;
                 if (h >= 0 && ((piece >> x) & 1)) m |= 1u << h;
             }
             t.push_back(m);
