@@ -191,7 +191,7 @@ __device__ __forceinline__ uint32_t b3_row_from_state(const uint32_t *const *st,
 // IN_BITS / OUT_BITS: the generation reads / writes the bit-packed states
 // a.b3.sin / a.b3.sout instead of bytes (single-instance launches).
 template <bool MULTI, bool B5S45, int KW, bool IN_BITS = false, bool OUT_BITS = false>
-__global__ void __launch_bounds__(32 * kB3Warps, 4)
+__global__ void __launch_bounds__(32 * kB3Warps, (IN_BITS && OUT_BITS && B5S45) ? 5 : 4)
 step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -199,9 +199,12 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
     for (int i = threadIdx.x; i < a.b3.nshared; i += blockDim.x) stab[i] = __ldg(a.tab + i);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint8_t *wb = smem + a.b3.off_warp + warp * a.b3.warp_bytes;
+    // states -> states needs no box and no result bits, only each warp's 27
+    // state pointers (kB3StatePtrBytes): five blocks fit per SM
+    constexpr bool kStatesOnly = IN_BITS && OUT_BITS;
+    uint8_t *wb = smem + a.b3.off_warp + warp * (kStatesOnly ? kB3StatePtrBytes : a.b3.warp_bytes);
     uint32_t *box = reinterpret_cast<uint32_t *>(wb);
-    const uint8_t **nbase = reinterpret_cast<const uint8_t **>(wb + kB3OffPtr);
+    const uint8_t **nbase = reinterpret_cast<const uint8_t **>(wb + (kStatesOnly ? 0 : kB3OffPtr));
     uint32_t *bits = reinterpret_cast<uint32_t *>(wb + kB3OffBits);
     const uint32_t *CT = stab, *RT = stab + a.b3.off_rt, *BP = stab + a.b3.off_bp, *HS = stab + a.b3.off_hs;
     const uint2 *HE = reinterpret_cast<const uint2 *>(stab + a.b3.off_he);

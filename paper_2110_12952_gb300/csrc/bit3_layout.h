@@ -17,6 +17,7 @@ constexpr int kB3OffBits = kB3OffPtr + 224;   // 27 pointers (the bit-state path
 // word (y - 1) + 27 (z - 1)), then its faces x = 0 and x = 26 as 27 words
 // each (word z: bit y = cell (0 or 26, y, z)); padded to 16 bytes.
 constexpr int kB3StateWords = 784;
+constexpr int kB3StatePtrBytes = 224;         // per warp in generations from states to states: 27 pointers
 constexpr int kB3StateXL = 729;
 constexpr int kB3StateXH = 756;
 

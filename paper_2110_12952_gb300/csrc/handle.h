@@ -25,6 +25,7 @@ struct Bit3Args {
     int nshared = 0;       // words copied to shared memory
     int off_warp = 0;      // byte offset of warp 0's area in shared memory
     int warp_bytes = 0;    // shared memory per warp (box, pointers, result bits)
+    int grid_states = 0;   // blocks per launch of the states -> states generations (smaller shared memory)
     const uint32_t *sin = nullptr;   // multi-generation runs: bit-packed input state (kB3StateWords per tile)
     uint32_t *sout = nullptr;        // and output state, or null
 };

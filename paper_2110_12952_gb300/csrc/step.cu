@@ -1014,6 +1014,9 @@ static int bit3_allow_smem(int optin)
     return FR_OK;
 }
 
+// shared memory of a states -> states generation: the tables and each warp's pointers
+static int bit3_states_smem(const StepPlan &p) { return p.b3.off_warp + kB3Warps * kB3StatePtrBytes; }
+
 // bit3 mode: eight tiles (warps) per block
 static int configure_bit3(StepPlan &p, int num_sms)
 {
@@ -1030,6 +1033,13 @@ static int configure_bit3(StepPlan &p, int num_sms)
     if (!rc) rc = bit3_allow_smem<true, 5>(optin);
     if (rc) return rc;
     FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_bit3_kernel<false, false, 0, false, false>, p.block, p.smem));
+    {
+        int per_sm_states = 0;
+        FR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_states, step_bit3_kernel<false, true, 5, true, true>,
+                                                              p.block, bit3_states_smem(p)));
+        p.b3.grid_states = (int)std::min<int64_t>((int64_t)std::max(per_sm_states, 1) * num_sms,
+                                                  (p.NT + kB3Warps - 1) / kB3Warps);
+    }
     if (per_sm < 1) {
         set_error(FR_EINVAL, "fractal_step: tile does not fit in shared memory");
         return FR_EINVAL;
@@ -2607,16 +2617,18 @@ template <bool IB, bool OB>
 static int launch_bit3_mode(const fractal *f, const StepArgs &a, const uint8_t *in, uint8_t *out, cudaStream_t st)
 {
     const StepPlan &p = f->plan;
-    const int grid = (int)std::min<int64_t>(p.grid, (a.NT + kB3Warps - 1) / kB3Warps);
+    const bool states_only = IB && OB;
+    const int grid = (int)std::min<int64_t>(states_only ? p.b3.grid_states : p.grid, (a.NT + kB3Warps - 1) / kB3Warps);
+    const int smem = states_only ? bit3_states_smem(p) : p.smem;
     const bool b5s45 = a.rule.birth == (1u << 5) && a.rule.survive == ((1u << 4) | (1u << 5));
     if (p.b3.k != 20 && b5s45)
-        step_bit3_kernel<false, true, 0, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+        step_bit3_kernel<false, true, 0, IB, OB><<<grid, p.block, smem, st>>>(a, in, out);
     else if (p.b3.k != 20)
-        step_bit3_kernel<false, false, 0, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+        step_bit3_kernel<false, false, 0, IB, OB><<<grid, p.block, smem, st>>>(a, in, out);
     else if (b5s45)
-        step_bit3_kernel<false, true, 5, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+        step_bit3_kernel<false, true, 5, IB, OB><<<grid, p.block, smem, st>>>(a, in, out);
     else
-        step_bit3_kernel<false, false, 5, IB, OB><<<grid, p.block, p.smem, st>>>(a, in, out);
+        step_bit3_kernel<false, false, 5, IB, OB><<<grid, p.block, smem, st>>>(a, in, out);
     FR_CUDA(cudaGetLastError());
     return FR_OK;
 }
