@@ -222,7 +222,7 @@ step_bit3_kernel(StepArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict
         const uint8_t *tin = t.in + t.T * KL;
         const int32_t tn = lane < 26 ? __ldg(t.nbr + t.T * a.nbrw + lane) : -1;
         if constexpr (IN_BITS) {
-                // 1-2. the states of the tile and its neighbours, by direction; the
+            // 1-2. the states of the tile and its neighbours, by direction; the
             // rows are read from them as the walk below needs them
             const uint32_t **st = reinterpret_cast<const uint32_t **>(nbase);
             const int32_t tq = __shfl_sync(0xffffffffu, tn, lane < 13 ? lane : lane - 1);   // direction lane -> slot
