@@ -5,16 +5,16 @@
 // Membership of a box cell factorises over levels: the cell is in the
 // fractal iff its lowest Lb base-s digits form a member of the level-Lb
 // fractal and its digits above Lb form a member of the level-(r-Lb) one.
-// Both are precomputed bitmaps (about sqrt of the box each), so a cell's
-// membership costs two divisions by s^Lb and two bit look-ups.
+// Both are precomputed bitmaps (about sqrt of the box each; the local one
+// stores each of its rows twice in a row, so that a run of up to S cells
+// starting anywhere in a local row reads as one bit field), so a cell's
+// membership costs two divisions by s^Lb = S and two bit look-ups.
 //
-// Three kernels: rows of 16 cells per lane walked down by a warp for 2D
-// boxes with s = 2 and aligned rows (bb_fast_kernel) and for other 2D and 3D
-// boxes whose local bitmap side is at least 16 (bb_rows_kernel,
-// bb_rows3_kernel); otherwise (small boxes, buffers not 16-byte aligned)
-// each CTA stages a tile of the box plus a one-cell halo in shared memory,
-// one byte per cell (bit 0 = alive member, bit 1 = member), and applies the
-// rule from there (bb_kernel).
+// Two kernels: bit-sliced rows (bb_bits2_kernel, bb_bits3_kernel, below)
+// for boxes of side >= 32 in 16-byte aligned buffers (S >= 32 then); other
+// boxes take bb_kernel, where each CTA stages a tile of the box plus a
+// one-cell halo in shared memory, one byte per cell (bit 0 = alive member,
+// bit 1 = member), and applies the rule from there.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,14 +46,19 @@ static bool host_member(const fractal *f, int64_t x, int64_t y, int64_t z, int l
     return true;
 }
 
-static int build_bitmap(const fractal *f, int side, int levels, int base, uint32_t **out, int64_t *words)
+// doubled: each row of `side` bits is followed by a copy of itself
+static int build_bitmap(const fractal *f, int side, int levels, int base, bool doubled, uint32_t **out, int64_t *words)
 {
-    int64_t n = ipow64(side, f->dim);
-    int64_t nw = (n + 31) / 32 + 1;   // one spare word: 32-bit windows may start in the last word
+    const int64_t n = ipow64(side, f->dim), rep = doubled ? 2 : 1;
+    const int64_t nw = (n * rep + 31) / 32 + 1;   // one spare word: 32-bit windows may start in the last word
     std::vector<uint32_t> bits(nw, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t x = i % side, y = (i / side) % side, z = f->dim == 3 ? i / ((int64_t)side * side) : 0;
-        if (host_member(f, x, y, z, levels, base)) bits[i >> 5] |= 1u << (i & 31);
+        if (!host_member(f, x, y, z, levels, base)) continue;
+        for (int64_t c = 0; c < rep; ++c) {
+            const int64_t b = (i / side) * side * rep + c * side + x;
+            bits[b >> 5] |= 1u << (b & 31);
+        }
     }
     FR_CUDA(cudaMalloc(out, nw * sizeof(uint32_t)));
     FR_CUDA(cudaMemcpy(*out, bits.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -76,8 +81,8 @@ int ensure_bb_plan(fractal *f)
     while (ipow64(f->s, p.Lb) < 32 && p.Lb < f->r) ++p.Lb;   // S >= 32 where the box allows (bit-sliced rows)
     p.S = (int)ipow64(f->s, p.Lb);
     p.C = (int)ipow64(f->s, f->r - p.Lb);
-    int rc = build_bitmap(f, p.S, p.Lb, 0, &p.local_bits, &p.local_words);
-    if (!rc) rc = build_bitmap(f, p.C, f->r - p.Lb, p.Lb, &p.coarse_bits, &p.coarse_words);
+    int rc = build_bitmap(f, p.S, p.Lb, 0, true, &p.local_bits, &p.local_words);
+    if (!rc) rc = build_bitmap(f, p.C, f->r - p.Lb, p.Lb, false, &p.coarse_bits, &p.coarse_words);
     if (rc) {
         free_bb_plan(p);
         return rc;
@@ -130,7 +135,7 @@ bb_kernel(BBArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
             if (gx >= 0 && gx < a.n && gy >= 0 && gy < a.n && gz >= 0 && gz < a.n) {
                 const uint32_t cx = divu(a.sdiv, gx), cy = divu(a.sdiv, gy), cz = divu(a.sdiv, gz);
                 const uint32_t lx = gx - cx * a.S, ly = gy - cy * a.S, lz = gz - cz * a.S;
-                const int64_t li = lx + (int64_t)a.S * (ly + (int64_t)a.S * lz);
+                const int64_t li = lx + 2 * (int64_t)a.S * (ly + (int64_t)a.S * lz);   // rows stored twice
                 const int64_t ci = cx + (int64_t)a.C * (cy + (int64_t)a.C * cz);
                 if (bit_at(a.local_bits, li) & bit_at(a.coarse_bits, ci)) {
                     const int64_t g = gx + n * (gy + n * (int64_t)gz);
@@ -161,217 +166,14 @@ bb_kernel(BBArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
     }
 }
 
-// ---------------------------------------------------------------------
-// Vectorised path for 2D boxes with s = 2 and n a multiple of 512: each lane
-// owns 16 consecutive bytes of a row, a warp 512 columns; the warp walks down
-// a strip of rows with the rows above, at and below in registers (two more
-// rows' loads in flight).  Left/right neighbour bytes come from the adjacent
-// lanes (shuffles) or, at the warp's edges, from single-byte loads.  Counts
-// are byte-wise sums (<= 9, no carries); the rule is a byte look-up (prmt).
-
-struct BBFastArgs {
-    int32_t n;            // box side
-    int Lb;               // levels of the local bitmap (S = 2^Lb >= 32)
-    int32_t C;            // coarse side n / S
-    const uint32_t *local_bits, *coarse_bits;
-    int rows;             // rows per warp strip
-    int strips_x;         // n / 512
-    int64_t warps;        // strips_x * ceil(n / rows)
-    Rule rule;
-};
-
-__device__ __forceinline__ uint32_t prmt_bb(uint32_t a, uint32_t b, uint32_t sel)
-{
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
 // 4 bits -> 4 bytes of 0/1 (bit i lands in bit 8i; the other partial
 // products fall on distinct non-multiples of 8, so nothing carries)
 __device__ __forceinline__ uint32_t nib_bytes(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
-
-__device__ __forceinline__ uint32_t nz_bytes(uint32_t v)
-{
-    return (((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) >> 7 & 0x01010101u;
-}
-
-// membership bits of the 16 cells starting at x0 (a multiple of 16) in row y
-__device__ __forceinline__ uint32_t member16(const BBFastArgs &a, int32_t x0, int32_t y)
-{
-    const uint32_t S = 1u << a.Lb;
-    const uint32_t bit = ((uint32_t)y & (S - 1)) * S + ((uint32_t)x0 & (S - 1));
-    const uint32_t m = (__ldg(a.local_bits + (bit >> 5)) >> (bit & 31)) & 0xffffu;
-    const uint32_t c = (uint32_t)(y >> a.Lb) * (uint32_t)a.C + (uint32_t)(x0 >> a.Lb);
-    return ((__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u) ? m : 0u;
-}
-
-__device__ __forceinline__ uint32_t member1(const BBFastArgs &a, int32_t x, int32_t y)
-{
-    const uint32_t S = 1u << a.Lb;
-    const uint32_t bit = ((uint32_t)y & (S - 1)) * S + ((uint32_t)x & (S - 1));
-    const uint32_t c = (uint32_t)(y >> a.Lb) * (uint32_t)a.C + (uint32_t)(x >> a.Lb);
-    return (__ldg(a.local_bits + (bit >> 5)) >> (bit & 31)) & (__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u;
-}
-
-struct RowRaw {
-    uint4 v;
-    uint32_t el, er;   // raw bytes left of the warp's first cell / right of its last
-};
-
-__device__ __forceinline__ RowRaw load_row(const BBFastArgs &a, const uint8_t *__restrict__ in,
-                                           int32_t x0, int32_t y, int lane)
-{
-    RowRaw r;
-    r.v = make_uint4(0, 0, 0, 0);
-    r.el = r.er = 0;
-    if (y >= 0 && y < a.n) {
-        const uint8_t *row = in + (int64_t)y * a.n;
-        r.v = __ldg(reinterpret_cast<const uint4 *>(row + x0));
-        if (lane == 0 && x0 > 0) r.el = __ldg(row + x0 - 1);
-        if (lane == 31 && x0 + 16 < a.n) r.er = __ldg(row + x0 + 16);
-    }
-    return r;
-}
-
-// Masked 0/1 bytes, member bytes and horizontal 3-sums of one row.
-struct RowOut {
-    uint32_t d[4], m[4], h[4];
-};
-
-__device__ __forceinline__ void process_row(const BBFastArgs &a, const RowRaw &r, int32_t x0,
-                                            int32_t y, int lane, RowOut &o)
-{
-    uint32_t m16 = 0, ml = 0, mr = 0;
-    if (y >= 0 && y < a.n) {
-        m16 = member16(a, x0, y);
-        if (lane == 0 && x0 > 0) ml = member1(a, x0 - 1, y);
-        if (lane == 31 && x0 + 16 < a.n) mr = member1(a, x0 + 16, y);
-    }
-    const uint32_t raw[4] = {r.v.x, r.v.y, r.v.z, r.v.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        o.m[q] = nib_bytes((m16 >> (4 * q)) & 0xfu);
-        o.d[q] = nz_bytes(raw[q]) & o.m[q];
-    }
-    uint32_t left = __shfl_up_sync(0xffffffffu, o.d[3], 1);    // byte 3 = cell x0 - 1
-    uint32_t right = __shfl_down_sync(0xffffffffu, o.d[0], 1); // byte 0 = cell x0 + 16
-    if (lane == 0) left = ((r.el != 0) & ml) << 24;
-    if (lane == 31) right = (r.er != 0) & mr;
-    const uint32_t w[6] = {left, o.d[0], o.d[1], o.d[2], o.d[3], right};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        o.h[q] = w[q + 1] + __funnelshift_l(w[q], w[q + 1], 8) + __funnelshift_r(w[q + 1], w[q + 2], 8);
-}
-
-__device__ __forceinline__ uint32_t rule4_bb(const uint32_t lut[4], uint32_t t, uint32_t alive)
-{
-    const uint32_t x = t | (t >> 4);
-    const uint32_t sel = prmt_bb(x, 0u, 0x3120u);
-    const uint32_t rd = prmt_bb(lut[0], lut[1], sel) & 0x01010101u;
-    const uint32_t rl = prmt_bb(lut[2], lut[3], sel) & 0x01010101u;
-    const uint32_t m = alive * 0xffu;
-    return (rl & m) | (rd & ~m);
-}
-
-__global__ void __launch_bounds__(128)
-bb_fast_kernel(BBFastArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (wid >= a.warps) return;   // whole warps leave together
-    const int32_t x0 = (int32_t)(wid % a.strips_x) * 512 + lane * 16;
-    const int32_t y0 = (int32_t)(wid / a.strips_x) * a.rows;
-    const int32_t y1 = min(y0 + a.rows, a.n);
-    RowOut up, mid, dn;
-    process_row(a, load_row(a, in, x0, y0 - 1, lane), x0, y0 - 1, lane, up);
-    process_row(a, load_row(a, in, x0, y0, lane), x0, y0, lane, mid);
-    RowRaw r1 = load_row(a, in, x0, y0 + 1, lane);
-    RowRaw r2 = load_row(a, in, x0, y0 + 2, lane);
-    for (int32_t y = y0; y < y1; ++y) {
-        process_row(a, r1, x0, y + 1, lane, dn);
-        r1 = r2;
-        r2 = load_row(a, in, x0, y + 3, lane);
-        uint32_t nw[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            nw[q] = rule4_bb(a.rule.lut, up.h[q] + mid.h[q] + dn.h[q], mid.d[q]) & mid.m[q];
-        *reinterpret_cast<uint4 *>(out + (int64_t)y * a.n + x0) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
-        up = mid;
-        mid = dn;
-    }
-}
-
-// ---------------------------------------------------------------------
-// Vectorised path for other 2D boxes whose local side S = s^Lb is at least
-// 16 (s = 3 from r = 5 on): the rows need not start 16-byte aligned.  Lane
-// l of a warp holds the 16 cells x0 = 480 sx + 16 l .. x0 + 15 of a row and
-// walks down a strip of rows as bb_fast_kernel does.  The cells' bytes sit
-// at flat offset f = y n + x0, and k = f mod 16 is the same in every lane
-// of the warp: each lane loads the aligned chunk at f - k, takes the next
-// one from the next lane, and shifts.  Membership of the 16 cells is a
-// 16-bit field of the local bitmap's row (split in two where the cells
-// cross into the next local tile, each part gated by its coarse bit); cells
-// past the row's end get no membership.
-//
-// Results go back as whole aligned 16-byte chunks: lane l (0..30) writes the
-// chunk after f - k, its own cells 16 - k .. 15 followed by lane l + 1's
-// cells 0 .. 15 - k (for k = 0: lanes 1..30 their own 16 cells).  Strips
-// advance by 480 cells, so lanes 0 and 31 overlap the neighbouring strips:
-// the cells they write never need the cell beyond them (lane 0 writes cells
-// from 16 - k >= 1 on, lane 31 up to 15 - k <= 14), which is why no lane
-// fetches cells outside its warp; the one chunk per strip boundary is
-// written by both warps with the same bytes.  The head of a row (strip 0,
-// lane 0, before its first chunk) and chunks reaching past the row's end
-// are written byte by byte.
-
-struct BBRowsArgs {
-    int32_t n;            // box side
-    int64_t total;        // n^2 bytes
-    int32_t S, C;         // local / coarse sides (S >= 16)
-    DivU32 sdiv;          // division by S
-    const uint32_t *local_bits, *coarse_bits;
-    int rows;             // rows per warp strip
-    int strips_x;         // strips per row (480 cells apart)
-    int64_t warps;        // strips_x * ceil(n / rows)
-    Rule rule;
-};
 
 // 32 bits of a bitmap from bit pos on (bitmaps carry one spare word)
 __device__ __forceinline__ uint32_t bits32_at(const uint32_t *__restrict__ bits, uint32_t pos)
 {
     return __funnelshift_r(__ldg(bits + (pos >> 5)), __ldg(bits + (pos >> 5) + 1), pos & 31);
-}
-
-__device__ __forceinline__ uint32_t coarse_bit(const BBRowsArgs &a, int32_t cx, int32_t cy, int32_t cz)
-{
-    if (cx >= a.C) return 0u;
-    const uint32_t c = ((uint32_t)cz * (uint32_t)a.C + (uint32_t)cy) * (uint32_t)a.C + (uint32_t)cx;
-    return (__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u;
-}
-
-// bytes k .. k + 15 of the 32 bytes w[0..7] (k the same in the whole warp)
-__device__ __forceinline__ void bytes16_at(const uint32_t w[8], int k, uint32_t d[4])
-{
-    const uint32_t sh = 8u * (uint32_t)(k & 3);
-    switch (k >> 2) {
-        case 0:
-#pragma unroll
-            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i], w[i + 1], sh);
-            break;
-        case 1:
-#pragma unroll
-            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i + 1], w[i + 2], sh);
-            break;
-        case 2:
-#pragma unroll
-            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i + 2], w[i + 3], sh);
-            break;
-        default:
-#pragma unroll
-            for (int i = 0; i < 4; ++i) d[i] = __funnelshift_r(w[i + 3], w[i + 4], sh);
-            break;
-    }
 }
 
 // the 16 bytes at in + a (a 16-byte aligned), 0 outside [0, total)
@@ -390,218 +192,6 @@ __device__ __forceinline__ uint4 load16_bounded(const uint8_t *__restrict__ in, 
     return make_uint4(w0, w1, w2, w3);
 }
 
-struct RowsRow {
-    uint32_t d[4], m[4], h[4];
-};
-
-// The lane's column constants, its plane (3D; plane 0 in 2D) and the row
-// it stands at: local and coarse row, and the coarse bits of its two
-// possible coarse columns there (refreshed when the coarse row changes).
-struct RowsCursor {
-    int32_t x0, xl0, cx0;
-    uint32_t mask1;       // cells of the first local tile
-    int first;            // S - xl0
-    bool live;            // the plane lies inside the box
-    int64_t plane;        // flat offset of the plane (z n^2)
-    int32_t zl, cz;       // local and coarse plane
-    int32_t yl, cy;       // of the next row to process
-    uint32_t c1, c2;      // coarse bits of columns cx0, cx0 + 1 in coarse row cy (and plane cz)
-};
-
-__device__ __forceinline__ void rows_cursor_row(const BBRowsArgs &a, RowsCursor &u, int32_t y)
-{
-    const uint32_t cy = divu(a.sdiv, (uint32_t)y);
-    u.yl = y - (int32_t)(cy * (uint32_t)a.S);
-    u.cy = (int32_t)cy;
-    u.c1 = coarse_bit(a, u.cx0, u.cy, u.cz);
-    u.c2 = u.first < 16 ? coarse_bit(a, u.cx0 + 1, u.cy, u.cz) : 0u;   // the second local tile only if the cells reach it
-}
-
-// a lane's cursor for strip x0, plane z (z = 0 in 2D), standing at row y
-__device__ __forceinline__ void rows_cursor_init(const BBRowsArgs &a, RowsCursor &u, int32_t x0, int32_t z, int32_t y)
-{
-    u.x0 = x0;
-    const uint32_t cx0 = divu(a.sdiv, (uint32_t)x0);
-    u.cx0 = (int32_t)cx0;
-    u.xl0 = x0 - (int32_t)(cx0 * (uint32_t)a.S);
-    u.first = a.S - u.xl0;
-    u.mask1 = u.first >= 16 ? 0xffffu : (1u << u.first) - 1u;
-    u.live = z >= 0 && z < a.n;
-    const int32_t zc = u.live ? z : 0;
-    u.plane = (int64_t)zc * a.n * a.n;
-    const uint32_t cz = divu(a.sdiv, (uint32_t)zc);
-    u.cz = (int32_t)cz;
-    u.zl = zc - (int32_t)(cz * (uint32_t)a.S);
-    rows_cursor_row(a, u, y);
-}
-
-// masked 0/1 bytes, member bytes and horizontal 3-sums of the lane's cells
-// in row y (zeros for rows outside the box); lane 0's left and lane 31's
-// right neighbour count as 0 (see above).  Rows come in increasing order,
-// the cursor standing at row y (for rows inside the box).
-__device__ __forceinline__ void rows_process(const BBRowsArgs &a, const uint8_t *__restrict__ in, RowsCursor &u,
-                                             int32_t y, int lane, RowsRow &o)
-{
-    const int32_t x0 = u.x0;
-    uint32_t raw[4] = {0u, 0u, 0u, 0u}, m16 = 0u;
-    if (u.live && y >= 0 && y < a.n) {   // the same in the whole warp
-        const int64_t f = u.plane + (int64_t)y * a.n + x0;
-        const int k = (int)(f & 15);
-        const int64_t a0 = f - k;
-        const uint4 c = load16_bounded(in, a.total, a0);
-        uint4 nx;
-        nx.x = __shfl_down_sync(0xffffffffu, c.x, 1);
-        nx.y = __shfl_down_sync(0xffffffffu, c.y, 1);
-        nx.z = __shfl_down_sync(0xffffffffu, c.z, 1);
-        nx.w = __shfl_down_sync(0xffffffffu, c.w, 1);
-        if (lane == 31) nx = load16_bounded(in, a.total, a0 + 16);
-        const uint32_t w[8] = {c.x, c.y, c.z, c.w, nx.x, nx.y, nx.z, nx.w};
-        bytes16_at(w, k, raw);
-        const uint32_t rowbit = ((uint32_t)u.zl * (uint32_t)a.S + (uint32_t)u.yl) * (uint32_t)a.S;
-        m16 = (u.c1 ? bits32_at(a.local_bits, rowbit + (uint32_t)u.xl0) & u.mask1 : 0u) |
-              (u.c2 ? (bits32_at(a.local_bits, rowbit) << (u.first & 31)) & 0xffffu : 0u);
-        if (++u.yl == a.S && y + 1 < a.n) rows_cursor_row(a, u, y + 1);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        o.m[q] = nib_bytes((m16 >> (4 * q)) & 0xfu);
-        o.d[q] = nz_bytes(raw[q]) & o.m[q];
-    }
-    uint32_t left = __shfl_up_sync(0xffffffffu, o.d[3], 1);    // byte 3 = cell x0 - 1
-    uint32_t right = __shfl_down_sync(0xffffffffu, o.d[0], 1); // byte 0 = cell x0 + 16
-    if (lane == 0) left = 0u;
-    if (lane == 31) right = 0u;
-    const uint32_t w[6] = {left, o.d[0], o.d[1], o.d[2], o.d[3], right};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        o.h[q] = w[q + 1] + __funnelshift_l(w[q], w[q + 1], 8) + __funnelshift_r(w[q + 1], w[q + 2], 8);
-}
-
-// The results of row y: lane l's chunk (see above), from its 16 result
-// bytes o; `row_end` is the flat offset of the row's end.
-__device__ __forceinline__ void rows_store(uint8_t *__restrict__ out, int64_t f, int64_t row_end, int32_t x0, int lane,
-                                           const uint32_t o[4])
-{
-    const int k = (int)(f & 15);
-    const uint32_t nx[4] = {__shfl_down_sync(0xffffffffu, o[0], 1), __shfl_down_sync(0xffffffffu, o[1], 1),
-                            __shfl_down_sync(0xffffffffu, o[2], 1), __shfl_down_sync(0xffffffffu, o[3], 1)};
-    const bool head = x0 == 0 && k != 0;   // strip 0, lane 0: the row's first bytes
-    const bool writer = k == 0 ? (lane >= 1 && lane <= 30) || x0 == 0 : lane <= 30;
-    uint32_t c[4];
-    int64_t p;
-    if (k == 0) {
-        c[0] = o[0]; c[1] = o[1]; c[2] = o[2]; c[3] = o[3];
-        p = f;
-    } else {
-        const uint32_t w[8] = {o[0], o[1], o[2], o[3], nx[0], nx[1], nx[2], nx[3]};
-        bytes16_at(w, 16 - k, c);
-        p = f - k + 16;
-    }
-    if (writer && p < row_end) {
-        if (p + 16 <= row_end) {
-            *reinterpret_cast<uint4 *>(out + p) = make_uint4(c[0], c[1], c[2], c[3]);
-        } else {
-            for (int j = 0; j < (int)(row_end - p); ++j) out[p + j] = (uint8_t)(c[j >> 2] >> (8 * (j & 3)));
-        }
-    }
-    if (head) {
-        const int nh = (int)min((int64_t)(16 - k), row_end - f);
-        for (int j = 0; j < nh; ++j) out[f + j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
-    }
-}
-
-__global__ void __launch_bounds__(128)
-bb_rows_kernel(BBRowsArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (wid >= a.warps) return;   // whole warps leave together
-    const int32_t y0 = (int32_t)(wid / a.strips_x) * a.rows;
-    const int32_t y1 = min(y0 + a.rows, a.n);
-    RowsCursor u;
-    rows_cursor_init(a, u, (int32_t)(wid % a.strips_x) * 480 + lane * 16, 0, max(y0 - 1, 0));
-    RowsRow up, mid, dn;
-    rows_process(a, in, u, y0 - 1, lane, up);
-    rows_process(a, in, u, y0, lane, mid);
-    for (int32_t y = y0; y < y1; ++y) {
-        rows_process(a, in, u, y + 1, lane, dn);
-        uint32_t nw[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            nw[q] = rule4_bb(a.rule.lut, up.h[q] + mid.h[q] + dn.h[q], mid.d[q]) & mid.m[q];
-        rows_store(out, (int64_t)y * a.n + u.x0, (int64_t)(y + 1) * a.n, u.x0, lane, nw);
-        up = mid;
-        mid = dn;
-    }
-}
-
-// The 3D box: a warp takes plane z and a strip of rows y0 .. y1 - 1 of 16
-// cells per lane, and keeps the rows' horizontal sums added over the planes
-// z - 1, z, z + 1 for rows y - 1, y, y + 1 (each step loads row y + 1 of
-// the three planes); their sum is the 27-cell total (<= 27, bytes), the
-// rule a shift of the survival or birth mask per cell.  Neighbouring planes
-// go to consecutive warps, so the rows they share are read from L2.
-__device__ __forceinline__ uint32_t rule27(uint32_t t, uint32_t alive, uint32_t birth, uint32_t live_mask)
-{
-    uint32_t r = 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint32_t tj = (t >> (8 * j)) & 0xffu, aj = (alive >> (8 * j)) & 1u;
-        r |= (((aj ? live_mask : birth) >> tj) & 1u) << (8 * j);
-    }
-    return r;
-}
-
-__global__ void __launch_bounds__(128)
-bb_rows3_kernel(BBRowsArgs a, const uint8_t *__restrict__ in, uint8_t *__restrict__ out)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (wid >= a.warps) return;   // whole warps leave together
-    const int32_t z = (int32_t)(wid % a.n);
-    const int64_t rest = wid / a.n;
-    const int32_t x0 = (int32_t)(rest % a.strips_x) * 480 + lane * 16;
-    const int32_t y0 = (int32_t)(rest / a.strips_x) * a.rows;
-    const int32_t y1 = min(y0 + a.rows, a.n);
-    const uint32_t live_mask = (a.rule.survive << 1) & 0x0ffffffeu, birth = a.rule.birth & 0x07ffffffu;
-    RowsCursor ua, ub, uc;   // planes z - 1, z, z + 1
-    rows_cursor_init(a, ua, x0, z - 1, max(y0 - 1, 0));
-    rows_cursor_init(a, ub, x0, z, max(y0 - 1, 0));
-    rows_cursor_init(a, uc, x0, z + 1, max(y0 - 1, 0));
-    // P: horizontal sums over the three planes; mid: row y of plane z
-    uint32_t pu[4], pm[4], pd[4];
-    RowsRow ra, rb, rc, mid;
-    rows_process(a, in, ua, y0 - 1, lane, ra);
-    rows_process(a, in, ub, y0 - 1, lane, rb);
-    rows_process(a, in, uc, y0 - 1, lane, rc);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) pu[q] = ra.h[q] + rb.h[q] + rc.h[q];
-    rows_process(a, in, ua, y0, lane, ra);
-    rows_process(a, in, ub, y0, lane, mid);
-    rows_process(a, in, uc, y0, lane, rc);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) pm[q] = ra.h[q] + mid.h[q] + rc.h[q];
-    for (int32_t y = y0; y < y1; ++y) {
-        rows_process(a, in, ua, y + 1, lane, ra);
-        rows_process(a, in, ub, y + 1, lane, rb);
-        rows_process(a, in, uc, y + 1, lane, rc);
-        uint32_t nw[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            pd[q] = ra.h[q] + rb.h[q] + rc.h[q];
-            nw[q] = rule27(pu[q] + pm[q] + pd[q], mid.d[q], birth, live_mask) & mid.m[q];
-        }
-        rows_store(out, ub.plane + (int64_t)y * a.n + x0, ub.plane + (int64_t)(y + 1) * a.n, x0, lane, nw);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            pu[q] = pm[q];
-            pm[q] = pd[q];
-            mid.d[q] = rb.d[q];
-            mid.m[q] = rb.m[q];
-        }
-    }
-}
-
 // Bit-sliced rows (bb_bits2_kernel, bb_bits3_kernel; local bitmap side S
 // >= 32, box side n >= 32, buffers 16-byte aligned).  A lane owns 32
 // consecutive cells x0 .. x0 + 31 of a row (x0 = xs + 32 lane, strips xs
@@ -609,8 +199,9 @@ bb_rows3_kernel(BBRowsArgs a, const uint8_t *__restrict__ in, uint8_t *__restric
 // aligned bytes at F + x0 - k (F the row's flat start, k = (F + xs) mod
 // 16, the same across the warp), turns each byte into "nonzero" with a
 // carry-free multiply, takes the next lane's word and shifts by k, and
-// masks with the cells' membership (local bitmap row & coarse bit, for at
-// most two local tiles since S >= 32).  Horizontal 3-sums are two bit
+// masks with the cells' membership (a 32-bit field of the doubled local
+// bitmap row, each part gated by its local tile's coarse bit: at most two
+// tiles since S >= 32).  Horizontal 3-sums are two bit
 // planes (full adder of the word and its two shifts), the 9 (2D) or 27 (3D)
 // cell totals bit-sliced adds of those, and the rule a sum over the totals
 // t it maps to "alive" of [total == t].  Results go out as aligned 16-byte
@@ -642,7 +233,7 @@ struct BBBitsArgs {
 
 struct BitsLane {
     int32_t xs, x0, cx0;
-    uint32_t xl0, first, mask1;    // first: cells in the first local tile
+    uint32_t xl0, mask1;           // mask1: the cells in the first local tile (S - xl0 of them)
 };
 
 __device__ __forceinline__ BitsLane bits_lane(const BBBitsArgs &a, int32_t sx, int lane)
@@ -653,8 +244,8 @@ __device__ __forceinline__ BitsLane bits_lane(const BBBitsArgs &a, int32_t sx, i
     const uint32_t cx = divu(a.sdiv, (uint32_t)l.x0);
     l.cx0 = (int32_t)cx;
     l.xl0 = (uint32_t)l.x0 - cx * (uint32_t)a.S;
-    l.first = (uint32_t)a.S - l.xl0;
-    l.mask1 = l.first >= 32 ? ~0u : (1u << l.first) - 1u;
+    const uint32_t first = (uint32_t)a.S - l.xl0;
+    l.mask1 = first >= 32 ? ~0u : (1u << first) - 1u;
     return l;
 }
 
@@ -683,14 +274,12 @@ __device__ __forceinline__ uint32_t coarse_at(const BBBitsArgs &a, uint32_t crow
     return in ? (__ldg(a.coarse_bits + (c >> 5)) >> (c & 31)) & 1u : 0u;
 }
 
-// membership of the lane's 32 cells in a row whose local bitmap row starts at
-// bit `rowbit`, given the coarse bits of the lane's two local tiles (bit 0:
-// tile cx0, bit 1: tile cx0 + 1)
+// membership of the lane's 32 cells in a row whose (doubled) local bitmap row
+// starts at bit `rowbit`, given the coarse bits of the lane's two local tiles
+// (bit 0: tile cx0, the cells of mask1; bit 1: tile cx0 + 1)
 __device__ __forceinline__ uint32_t member32(const BBBitsArgs &a, const BitsLane &l, uint32_t rowbit, uint32_t cbits)
 {
-    const uint32_t w1 = bits32_at(a.local_bits, rowbit + l.xl0) & l.mask1;
-    const uint32_t w2 = l.first < 32 ? bits32_at(a.local_bits, rowbit) << l.first : 0u;
-    return ((cbits & 1u) ? w1 : 0u) | ((cbits & 2u) ? w2 : 0u);
+    return bits32_at(a.local_bits, rowbit + l.xl0) & (((cbits & 1u) ? l.mask1 : 0u) | ((cbits & 2u) ? ~l.mask1 : 0u));
 }
 
 // the coarse bits of the lane's two local tiles in the coarse row starting at bit `crow`
@@ -823,7 +412,7 @@ __device__ __forceinline__ void bits_rows(const BBBitsArgs &a, const uint8_t *__
         if (live) {
             const uint32_t cy = divu(a.sdiv, (uint32_t)yj);
             const uint32_t yl = (uint32_t)yj - cy * (uint32_t)a.S;
-            m[j] = member32(a, l, (p.lrow + yl) * (uint32_t)a.S,
+            m[j] = member32(a, l, (p.lrow + yl) * (uint32_t)(2 * a.S),
                             CACHED ? (cb >> (2 * j)) & 3u : coarse2(a, l, (p.crow + cy) * (uint32_t)a.C));
         } else {
             m[j] = 0u;
@@ -1031,48 +620,6 @@ int launch_bb_once(fractal *f, const uint8_t *in, uint8_t *out, uint32_t birth,
             bb_bits2_kernel<kRuleB3S23><<<(unsigned)grid, 128, 0, st>>>(a, in, out);
         else
             bb_bits2_kernel<kRuleAny><<<(unsigned)grid, 128, 0, st>>>(a, in, out);
-        FR_CUDA(cudaGetLastError());
-        return FR_OK;
-    }
-    if (f->dim == 2 && f->s == 2 && f->side >= 512 && f->side % 512 == 0 && f->bb.Lb >= 5 &&
-        ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
-        BBFastArgs a;
-        a.n = (int32_t)f->side;
-        a.Lb = f->bb.Lb;
-        a.C = f->bb.C;
-        a.local_bits = f->bb.local_bits;
-        a.coarse_bits = f->bb.coarse_bits;
-        a.rows = 64;
-        a.strips_x = a.n / 512;
-        a.warps = (int64_t)a.strips_x * ((a.n + a.rows - 1) / a.rows);
-        make_rule(birth, survive, &a.rule);
-        const int64_t grid = (a.warps + 3) / 4;
-        bb_fast_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
-        FR_CUDA(cudaGetLastError());
-        return FR_OK;
-    }
-    if (f->bb.S >= 16 && f->side >= 16 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) {
-        const BBPlan &p = f->bb;
-        BBRowsArgs a;
-        a.n = (int32_t)f->side;
-        a.total = (int64_t)f->side * f->side * (f->dim == 3 ? f->side : 1);
-        a.S = p.S;
-        a.C = p.C;
-        a.sdiv = make_div((uint32_t)p.S);
-        a.local_bits = p.local_bits;
-        a.coarse_bits = p.coarse_bits;
-        a.rows = 64;
-        // strip sx writes up to cell 480 sx + 512 - k (k < 16) and the head
-        // of strip 0 from cell 0: ceil((n - 16) / 480) + 1 strips cover a row
-        a.strips_x = (a.n > 496) ? (a.n - 496 + 479) / 480 + 1 : 1;
-        if (f->dim == 3) a.rows = 32;
-        a.warps = (int64_t)a.strips_x * ((a.n + a.rows - 1) / a.rows) * (f->dim == 3 ? a.n : 1);
-        make_rule(birth, survive, &a.rule);
-        const int64_t grid = (a.warps + 3) / 4;
-        if (f->dim == 3)
-            bb_rows3_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
-        else
-            bb_rows_kernel<<<(unsigned)grid, 128, 0, st>>>(a, in, out);
         FR_CUDA(cudaGetLastError());
         return FR_OK;
     }

@@ -4,7 +4,8 @@ evaluated with constants (B5/S45) and in general, non-binary input, other 3D
 tables whose replica counts are multiples of 4 (and a permuted replica
 order), buffers at unaligned addresses, tile ranges (the chunked host call),
 a batch of instances with different rules, the bit-packed state between the
-generations of a multi-generation call, and the plan it is chosen for."""
+generations of a multi-generation call, the plan it is chosen for, and the
+3D bounding-box row kernel on the same tables."""
 import numpy as np
 import pytest
 import torch
@@ -148,8 +149,8 @@ def test_bit_packed_generations(P, fam, r, rule):
 
 
 @pytest.mark.parametrize("fam,r", [(EDGES12, 5), (CORNERS8, 5), (DENSE24, 5)], ids=lambda v: getattr(v, "name", str(v)))
-def test_bb_rows3_other_tables(P, fam, r):
-    # the 3D row kernel of the bounding-box step on tables other than the Menger sponge's
+def test_bb_bits3_other_tables(P, fam, r):
+    # the 3D bit-sliced row kernel of the bounding-box step on tables other than the Menger sponge's
     g, o = pair(P, fam, r)
     rng = np.random.default_rng(r)
     box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)

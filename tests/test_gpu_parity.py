@@ -284,8 +284,8 @@ def test_bb_exhaustive_with_garbage(P, fam, r):
 
 
 @pytest.mark.parametrize("fam,r", [(W.TRIANGLE, 10), (W.TRIANGLE_MIRRORED, 9), (W.FULL_SQUARE, 9)])
-def test_bb_vectorised_path_with_garbage(P, fam, r):
-    # s = 2 boxes of side >= 512 take the 16-bytes-per-lane path
+def test_bb_bits_path_s2_with_garbage(P, fam, r):
+    # s = 2 boxes (16-byte aligned rows) take the bit-sliced row path
     g, o = gpu_fr(P, fam, r), ora(fam, r)
     rng = np.random.default_rng(r)
     box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
@@ -298,9 +298,9 @@ def test_bb_vectorised_path_with_garbage(P, fam, r):
 @pytest.mark.parametrize("fam,r", [(W.CARPET, 5), (W.CARPET, 6), (W.VICSEK, 6), (W.H_FRACTAL, 5), (W.X_FRACTAL, 6),
                                    (W.TRIANGLE, 7), (W.TRIANGLE_MIRRORED, 8)],
                          ids=lambda v: getattr(v, "name", str(v)))
-def test_bb_rows_path_with_garbage(P, fam, r):
-    # 2D boxes whose rows are not 16-byte aligned (local bitmap side >= 16)
-    # take the row-walking path; garbage and non-binary bytes off the fractal
+def test_bb_bits_path_with_garbage(P, fam, r):
+    # 2D boxes of side >= 32, rows not 16-byte aligned, take the bit-sliced
+    # row path; garbage and non-binary bytes off the fractal
     g, o = gpu_fr(P, fam, r), ora(fam, r)
     rng = np.random.default_rng(100 + r)
     box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
@@ -317,8 +317,8 @@ def test_bb_rows_path_with_garbage(P, fam, r):
 
 
 @pytest.mark.parametrize("rule", [W.MENGER_B5S45, (0x6, 0x1E)], ids=lambda r: f"B{r[0]:x}S{r[1]:x}")
-def test_bb_rows3_path_menger_r5_with_garbage(P, rule):
-    # 3D boxes with a local bitmap side >= 16 take the plane-walking row path
+def test_bb_bits3_path_menger_r5_with_garbage(P, rule):
+    # 3D boxes of side >= 32 take the plane-walking bit-sliced row path
     g, o = gpu_fr(P, W.MENGER, 5), ora(W.MENGER, 5)
     rng = np.random.default_rng(55)
     box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
@@ -329,7 +329,7 @@ def test_bb_rows3_path_menger_r5_with_garbage(P, rule):
         assert np.array_equal(out.cpu().numpy(), o.bb_step(box, rule=orl, steps=steps)), steps
 
 
-def test_bb_rows3_path_menger_r6_against_compact(P):
+def test_bb_bits3_path_menger_r6_against_compact(P):
     g, o = gpu_fr(P, W.MENGER, 6), ora(W.MENGER, 6)
     x = g.init_bernoulli(6, 0.5)
     init = x.cpu().numpy()
@@ -342,13 +342,47 @@ def test_bb_rows3_path_menger_r6_against_compact(P):
     assert np.array_equal(got[idx], want[idx])
 
 
-def test_bb_rows_path_carpet_r8_whole_box(P):
+def test_bb_bits_path_carpet_r8_whole_box(P):
     g, o = gpu_fr(P, W.CARPET, 8), ora(W.CARPET, 8)
     init = o.init_bernoulli(9, 0.5)
     box = o.scatter(init)
     out = g.bb_step(torch.from_numpy(box).cuda(), steps=2)
     assert np.array_equal(out.cpu().numpy(), o.bb_step(box, steps=2))
     assert np.array_equal(g.gather(out).cpu().numpy(), o.step(init, steps=2))
+
+
+def test_bb_bits_path_three_strips_carpet_r7(P):
+    # side 2187: three strips of 992 cells per row, garbage off the fractal
+    g, o = gpu_fr(P, W.CARPET, 7), ora(W.CARPET, 7)
+    rng = np.random.default_rng(77)
+    box = rng.integers(0, 3, size=g.box_cells).astype(np.uint8) * rng.integers(1, 200, size=g.box_cells).astype(np.uint8)
+    for rule in (W.LIFE_B3S23, (0x6, 0x1E)):
+        orl = oracle.Rule([i for i in range(9) if (rule[0] >> i) & 1], [i for i in range(9) if (rule[1] >> i) & 1])
+        out = g.bb_step(torch.from_numpy(box).cuda(), steps=2, rule=rule)
+        assert np.array_equal(out.cpu().numpy(), o.bb_step(box, rule=orl, steps=2)), rule
+
+
+TETRA4 = W.Family("tetra4", 4, 2, 3, ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)))
+
+
+def test_bb_bits3_path_two_strips_side_1024(P):
+    # a 3D box of side 1024 (two strips per row, 1.07e9 cells) with garbage
+    # off the fractal: its members against the oracle's compact step, and
+    # nothing alive off the fractal
+    g, o = gpu_fr(P, TETRA4, 10), ora(TETRA4, 10)
+    init = o.init_bernoulli(13, 0.5)
+    x = torch.from_numpy(init).cuda()
+    member = g.scatter(torch.ones_like(x)).bool()
+    box = torch.randint(0, 256, (g.box_cells,), dtype=torch.uint8, device="cuda")
+    box = torch.where(member, g.scatter(x), box)
+    del member
+    rule = (0x6, 0x1E)
+    orl = oracle.Rule([1, 2], [1, 2, 3, 4])
+    out = g.bb_step(box, steps=1, rule=rule)
+    del box
+    got = g.gather(out)
+    assert int(torch.count_nonzero(out)) == int(torch.count_nonzero(got))
+    assert np.array_equal(got.cpu().numpy(), o.step(init, rule=orl, steps=1))
 
 
 def test_scatter_gather_roundtrip(P):
