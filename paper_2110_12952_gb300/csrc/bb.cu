@@ -201,10 +201,11 @@ __device__ __forceinline__ uint4 load16_bounded(const uint8_t *__restrict__ in, 
 // carry-free multiply, takes the next lane's word and shifts by k, and
 // masks with the cells' membership (a 32-bit field of the doubled local
 // bitmap row, each part gated by its local tile's coarse bit: at most two
-// tiles since S >= 32).  Horizontal 3-sums are two bit
-// planes (full adder of the word and its two shifts), the 9 (2D) or 27 (3D)
-// cell totals bit-sliced adds of those, and the rule a sum over the totals
-// t it maps to "alive" of [total == t].  Results go out as aligned 16-byte
+// tiles since S >= 32).  Horizontal 3-sums are two bit planes (full adder of
+// the word and its two shifts), the 9 (2D) or 27 (3D) cell totals
+// bit-sliced adds of those, and the rule a closed form of the total's bits
+// for B3/S23 (2D) and B5/S45 (3D), else a sum over the totals t it maps to
+// "alive" of [total == t].  Results go out as aligned 16-byte
 // chunks: lane l (0 .. 30) writes the 32 bytes from F + x0 - k + 16 (its
 // cells 16 - k .. 31 and the next lane's first ones), which never needs
 // lane 0's cell x0 - 1 (unknown unless xs = 0) nor lane 31's last cells
